@@ -1,0 +1,157 @@
+"""Pins for the oracle's SSO run (Eq. 2.1, Alg. 2-4).
+
+Special cases that reduce to closed forms, invariants of the algorithm, the
+synchronous-generation property of Alg. 2, binomial branch frequencies, and a
+brute-force grid search at D <= 2.  Each piece the checks lean on (Philox rho
+words, fresh values, fitness) is pinned in its own test module."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+
+def _run(fn="sphere", N=16, D=6, t=5, Cg=0.4, Cp=0.7, Cw=0.9, lattice="f64", seed=1,
+         sid=0, nthreads=1):
+    p = workload.problem(fn, N, D, seed=seed, lattice=lattice, Cg=Cg, Cp=Cp, Cw=Cw,
+                         stream=sid)
+    r = oracle.run(fn, N, D, p["lb"], p["ub"], Cg, Cp, Cw, seed, t, lattice=lattice, sid=sid,
+                   o=p["o"], w=p["w"], M=p["M"], nthreads=nthreads)
+    return p, r
+
+
+def test_generation0_is_fresh_population():
+    p, r = _run(t=0, N=5, D=7)
+    for i in range(5):
+        for j in range(7):
+            assert r["X"][i, j] == oracle.fresh("f64", 1, 0, oracle.TAG_INIT, 0, i, j,
+                                                p["lb"], p["ub"])
+    assert np.array_equal(r["X"], r["P"])
+    f = np.array([oracle.fitness("sphere", r["X"][i], p["o"]) for i in range(5)])
+    assert np.array_equal(r["pF"], f)
+    assert r["log_b"][0] == int(np.argmin(f)) and r["log_acc"][0] == 5
+
+
+def test_cg_one_copies_gbest_everywhere():
+    """Cg = 1: every variable takes gBest_j (first branch of Eq. 2.1)."""
+    p0, r0 = _run(t=0, Cg=1.0, Cp=1.0, Cw=1.0)
+    p1, r1 = _run(t=1, Cg=1.0, Cp=1.0, Cw=1.0)
+    G0 = r0["P"][r0["log_b"][0]]
+    assert np.array_equal(r1["X"], np.tile(G0, (16, 1)))
+    assert np.array_equal(r1["P"], np.tile(G0, (16, 1)))      # f(G0) = min pF -> all accept
+    assert r1["log_acc"][1] == 16
+
+
+def test_cp_one_keeps_pbest_and_accepts_ties():
+    """Cg = 0, Cp = 1: X takes pBest; equal fitness is accepted ("<=", Alg. 3)."""
+    p0, r0 = _run(t=0, Cg=0.0, Cp=1.0, Cw=1.0)
+    p, r = _run(t=6, Cg=0.0, Cp=1.0, Cw=1.0)
+    assert np.array_equal(r["X"], r0["X"])
+    assert np.all(r["log_acc"] == 16)
+    assert np.all(r["log_v"] == r0["log_v"][0])
+
+
+@pytest.mark.parametrize("lattice", ["f64", "f32"])
+def test_cw_zero_is_pure_random_search(lattice):
+    """Cw = 0: every variable is fresh; pBest is the best position seen so far."""
+    N, D, T = 8, 5, 6
+    snaps = [_run(t=g, N=N, D=D, Cg=0.0, Cp=0.0, Cw=0.0, lattice=lattice)[1] for g in range(T + 1)]
+    p = _run(t=0, N=N, D=D, lattice=lattice)[0]
+    for g in range(1, T + 1):
+        X = snaps[g]["X"]
+        for i in range(N):
+            for j in range(D):
+                assert X[i, j] == oracle.fresh(lattice, 1, 0, oracle.TAG_FRESH, g, i, j,
+                                               p["lb"], p["ub"])
+    fx = np.array([[oracle.fitness("sphere", s["X"][i], p["o"]) for i in range(N)] for s in snaps])
+    assert np.array_equal(snaps[T]["pF"], fx.min(axis=0))
+
+
+def test_stepwise_update_reads_previous_generation():
+    """Alg. 2 is synchronous: at generation g every branch of Eq. 2.1 reads the
+    gBest / pBest / X of generation g-1, whatever other particles did in g."""
+    N, D = 12, 9
+    prev = _run(t=3, N=N, D=D)[1]
+    p, cur = _run(t=4, N=N, D=D)
+    Tg, Tp, Tw = (int(round(c * 2**32)) for c in (0.4, 0.7, 0.9))
+    G = prev["G"]
+    for i in range(N):
+        for j in range(D):
+            r = oracle.rho(1, 0, 4, i, j)
+            x = cur["X"][i, j]
+            if r < Tg:
+                assert x == G[j]
+            elif r < Tp:
+                assert x == prev["P"][i, j]
+            elif r < Tw:
+                assert x == prev["X"][i, j]
+            else:
+                assert x == oracle.fresh("f64", 1, 0, oracle.TAG_FRESH, 4, i, j, p["lb"], p["ub"])
+
+
+@pytest.mark.parametrize("fn", ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley",
+                                "rot_rastrigin"])
+@pytest.mark.parametrize("lattice", ["f64", "f32"])
+def test_invariants(fn, lattice):
+    N, D, t = 24, 11, 40
+    p, r = _run(fn, N=N, D=D, t=t, lattice=lattice, seed=3)
+    v = r["log_v"]
+    assert np.all(np.diff(v) <= 0)                             # gBest never worsens
+    assert np.all((r["X"] >= p["lb"]) & (r["X"] <= p["ub"]))    # positions stay in bounds
+    b = r["log_b"][t]
+    assert b == int(np.argmin(r["pF"]))                        # lowest-index arg-min
+    assert np.array_equal(r["G"], r["P"][b])
+    f = np.array([oracle.fitness(fn, r["P"][i], p["o"], p["w"], p["M"]) for i in range(N)])
+    assert np.array_equal(f, r["pF"])                          # pF is f(pBest)
+    if lattice == "f32":
+        assert np.all(r["X"].astype(np.float32).astype(np.float64) == r["X"])
+    # pBest fitness per particle never worsens: compare against a shorter run.
+    _, r2 = _run(fn, N=N, D=D, t=t // 2, lattice=lattice, seed=3)
+    assert np.all(r["pF"] <= r2["pF"])
+
+
+def test_branch_frequencies_binomial():
+    N, D, t = 50, 40, 50
+    _, r = _run(N=N, D=D, t=t)
+    n = N * D * t
+    probs = np.array([0.4, 0.3, 0.2, 0.1])
+    for k in range(4):
+        mu, sd = n * probs[k], np.sqrt(n * probs[k] * (1 - probs[k]))
+        assert abs(r["branch"][k] - mu) <= 5 * sd, (k, r["branch"][k], mu)
+
+
+def test_openmp_is_bit_identical():
+    p, a = _run("rastrigin", N=64, D=33, t=20, lattice="f32")
+    _, b = _run("rastrigin", N=64, D=33, t=20, lattice="f32", nthreads=4)
+    for k in ("X", "P", "pF", "G", "log_b", "log_v", "log_acc", "branch"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_streams_are_independent():
+    _, a = _run(N=8, D=8, t=3, sid=0)
+    _, b = _run(N=8, D=8, t=3, sid=1)
+    assert not np.array_equal(a["X"], b["X"])
+
+
+@pytest.mark.parametrize("fn", ["sphere", "rastrigin", "ackley"])
+@pytest.mark.parametrize("D", [1, 2])
+def test_bruteforce_grid(fn, D):
+    """D <= 2: the SSO gBest can never beat the true minimum (a dense grid minus
+    a Lipschitz margin), and after enough generations it is close to it."""
+    lb, ub = -2.0, 2.0
+    o = workload.shift(D, -1.5, 1.5, 4)
+    n = 801 if D == 1 else 201
+    axis = np.linspace(lb, ub, n)
+    h = axis[1] - axis[0]
+    if D == 1:
+        grid = [np.array([a]) for a in axis]
+    else:
+        grid = [np.array([a, b]) for a in axis for b in axis]
+    gmin = min(oracle.fitness(fn, x, o) for x in grid)
+    lip = {"sphere": 2 * 4.0 * np.sqrt(D), "rastrigin": (2 * 4.0 + 20 * np.pi) * np.sqrt(D),
+           "ackley": 60.0 * np.sqrt(D)}[fn]
+    r = oracle.run(fn, 40, D, lb, ub, 0.4, 0.7, 0.9, 2, 400, o=o)
+    best = r["log_v"][-1]
+    assert best >= gmin - lip * h * np.sqrt(D) / 2 - 1e-12
+    assert best >= 0.0                                          # the true minimum is 0 at o
+    assert best <= gmin + 0.05 * max(1.0, gmin) + 0.05
