@@ -1,0 +1,225 @@
+/*
+ * psso.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of
+ * Parallel Simplified Swarm Optimization (PSSO; Yeh, Liu, Tan, Huang,
+ * arXiv 2110.01470): one SSO generation over a whole swarm, i.e.
+ *   (a) the per-variable stepwise update of Eq. 2.1,
+ *   (b) the fitness of every particle (Kernel Function (E), Sec. 2.3.2;
+ *       test functions of Table 3.2 in shifted / rotated form),
+ *   (c) the pBest update (Alg. 3) and the gBest arg-min (Alg. 4),
+ * repeated for t synchronous generations (Alg. 2), for one swarm or for many
+ * independent swarms in one persistent launch.
+ *
+ * Conventions
+ *   * Every call returns a psso_status; nothing aborts or throws across the ABI.
+ *     psso_last_error() returns a message for the calling thread's last failure.
+ *   * The library owns all device memory it allocates.  Caller buffers are host
+ *     pointers unless stated otherwise; they are copied in (create) or out
+ *     (best, get_state, get_log) and never retained.
+ *   * Work is enqueued on the handle's CUDA stream (psso_config.stream, NULL =
+ *     the legacy default stream).  psso_run returns once the work is enqueued;
+ *     device-side failures (e.g. PSSO_ERR_TIMEOUT) surface at the next call that
+ *     synchronises (psso_sync, psso_best, psso_get_state, psso_get_log,
+ *     psso_save) or at the next psso_run.
+ *   * A handle may be used from one host thread at a time.
+ *
+ * Semantics (the readings of the paper this library implements; identical to
+ * the CPU oracle shipped with the tests):
+ *   * Eq. 2.1 with cumulative thresholds Cg <= Cp <= Cw in [0,1]: a 32-bit
+ *     Philox-4x32-10 word r per variable picks gBest_j if r < T(Cg), pBest_ij if
+ *     r < T(Cp), keeps x_ij if r < T(Cw), else a fresh uniform value in [lb,ub],
+ *     with T(C) = round-half-even(C * 2^32).
+ *   * Draws are keyed by (seed, stream_id) with counter (variable block,
+ *     particle, generation, tag); the result of a run depends on nothing else
+ *     (not on the launch shape, the GPU, or how generations are split between
+ *     psso_run calls).
+ *   * Generation 0 (the initial population, Kernel Function (I), Sec. 2.3.1)
+ *     is enqueued by psso_create / psso_create_ex; psso_run(h, t) then runs
+ *     generations g+1 .. g+t.
+ *   * pBest_i <- x_i when f(x_i) <= f(pBest_i) (Alg. 3); gBest is the
+ *     lowest-index arg-min of the pBest fitness (Alg. 4).
+ */
+#ifndef PSSO_H
+#define PSSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psso_ctx* psso_handle;
+
+typedef enum {
+    PSSO_OK = 0,
+    PSSO_ERR_ARG = 1,         /* invalid argument; nothing was changed            */
+    PSSO_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has details)  */
+    PSSO_ERR_OOM = 3,         /* device memory allocation failed                   */
+    PSSO_ERR_TIMEOUT = 4,     /* a cross-block wait ran past its limit; the handle
+                                 is left in an undefined state and must be destroyed
+                                 or reloaded with psso_load                          */
+    PSSO_ERR_STATE = 5,       /* call not valid in the handle's current state       */
+    PSSO_ERR_UNSUPPORTED = 6  /* valid request this build does not implement        */
+} psso_status;
+
+/* Test functions (Table 3.2 of the paper; shifted by o, rotated by M).
+ * z = x - o (or z = M (x - o) for the rotated forms):
+ *   SPHERE        sum z_j^2
+ *   ELLIPSOID     sum w_j z_j^2            (w given, e.g. 10^(6j/(D-1)))
+ *   RASTRIGIN     10 D + sum (z_j^2 - 10 cos(2 pi z_j))
+ *   ROSENBROCK    sum_{j<D-1} 100 (a_{j+1} - a_j^2)^2 + (a_j - 1)^2,  a = z + 1
+ *   ACKLEY        -20 exp(-0.2 sqrt(sum z^2 / D)) - exp(sum cos(2 pi z) / D) + 20 + e
+ * Every function is 0 at x = o. */
+typedef enum {
+    PSSO_SPHERE = 0,
+    PSSO_ELLIPSOID = 1,
+    PSSO_RASTRIGIN = 2,
+    PSSO_ROSENBROCK = 3,
+    PSSO_ACKLEY = 4,
+    PSSO_ROT_ELLIPSOID = 5,
+    PSSO_ROT_RASTRIGIN = 6,
+    PSSO_ROT_ACKLEY = 7
+} psso_fn;
+
+/* Position lattice: which grid fresh values (Eq. 2.1's last branch and the
+ * initial population) are drawn on.
+ *   F64: x = fma(ub - lb, m 2^-53, lb), m = 53 random bits.
+ *   F32: x = fmaf(S, m 2^-24, L) clamped to the floats inside [lb, ub], with
+ *        S, L the nearest floats to ub - lb and lb, m = 24 random bits.  Every
+ *        position is then a float, so FP32 and FP64 fitness see the same x. */
+typedef enum { PSSO_LATTICE_F64 = 0, PSSO_LATTICE_F32 = 1 } psso_lattice;
+
+/* Fitness precision.
+ *   F64          fitness in FP64 in a fixed summation order; results are
+ *                bit-identical to the CPU oracle.
+ *   F32_RECHECK  fitness in FP32 with a rigorous per-evaluation error bound;
+ *                every pBest / gBest comparison the bound cannot decide is
+ *                re-evaluated in FP64 (oracle order), so all decisions -- and
+ *                therefore all positions -- equal the F64 run's.  Needs the F32
+ *                lattice and a float-exact shift. */
+typedef enum { PSSO_PREC_F64 = 0, PSSO_PREC_F32_RECHECK = 1 } psso_precision;
+
+/* One problem instance (one independent swarm). */
+typedef struct {
+    int32_t fn;          /* psso_fn                                                */
+    int32_t lattice;     /* psso_lattice                                           */
+    int64_t N;           /* particles, 1 .. 2^31-1                                  */
+    int64_t D;           /* variables, 1 .. 1024                                    */
+    double lb, ub;       /* search bounds, lb < ub, finite                          */
+    double Cg, Cp, Cw;   /* cumulative Eq. 2.1 thresholds, 0 <= Cg <= Cp <= Cw <= 1 */
+    uint64_t seed;       /* Philox key                                              */
+    uint32_t stream_id;  /* Philox counter stream, < 2^24 (independent instances)   */
+    uint32_t reserved;   /* must be 0                                               */
+    const double* shift;    /* host, D values, or NULL for o = 0                    */
+    const double* weights;  /* host, D values; required by the ellipsoid functions  */
+    const double* rotation; /* host, D*D row-major M; required by rotated functions */
+} psso_problem;
+
+/* Launch and bookkeeping options; zero-initialise for the defaults. */
+typedef struct {
+    int32_t precision;          /* psso_precision                                   */
+    int32_t threads_per_block;  /* 0 = 256; a multiple of 32 in [64, 1024]          */
+    int32_t single_block_max;   /* 0 = auto: swarms of at most this many particle
+                                   passes run in one block with no cross-block
+                                   exchange; -1 = never                            */
+    int32_t log_stride;         /* log every log_stride-th generation (0 = off)     */
+    int64_t log_capacity;       /* log entries kept per instance (ring)             */
+    int64_t spin_limit;         /* polls of a cross-block wait before the run fails
+                                   with PSSO_ERR_TIMEOUT (0 = default, ~seconds)     */
+    void* stream;               /* cudaStream_t to enqueue on (NULL = default)      */
+    int32_t max_blocks;         /* 0 = all co-resident blocks; else an upper bound  */
+    int32_t fault_skip_rank;    /* testing only: 0 = off; k > 0 makes block rank k-1
+                                   of instance 0 never publish, so its peers' waits
+                                   run out and psso_run reports PSSO_ERR_TIMEOUT     */
+} psso_config;
+
+/* One log entry (psso_get_log). */
+typedef struct {
+    int64_t generation;
+    int64_t index;       /* gBest particle index                                    */
+    double value;        /* gBest fitness in FP64 (NaN if only the FP32 bounds are
+                            known at that generation)                              */
+    float value_lo;      /* rigorous lower / upper bound of the gBest fitness       */
+    float value_hi;
+    int64_t accepted;    /* pBest updates in this generation (all particles)        */
+    int64_t rechecks;    /* FP64 re-evaluations in this generation                  */
+} psso_log_entry;
+
+/* Counters since creation (psso_stats). */
+typedef struct {
+    int64_t generations;     /* generations completed (excluding generation 0)     */
+    int64_t evaluations;     /* fitness evaluations, all instances                  */
+    int64_t updates;         /* particle-variable updates, all instances            */
+    int64_t rechecks;        /* FP64 re-evaluations (F32_RECHECK)                   */
+    int32_t blocks;          /* blocks of the persistent launch                     */
+    int32_t threads_per_block;
+    int32_t instances;
+    int32_t reserved;
+} psso_stats_t;
+
+/* Creates one swarm with the zero shift, FP64 lattice and FP64 precision,
+ * and enqueues generation 0 on the default stream.  Ellipsoid weights are
+ * 10^(6 j/(D-1)).  Rotated functions need psso_create_ex (they need M).
+ * Paper: Sec. 3.3 (problem f on [L,U] with Nvar variables and Nsol particles),
+ * Table 3.1 (Sol, PBests, GBest, Cw/Cp/Cg, [varMin, varMax]). */
+psso_status psso_create(psso_fn fn, int64_t N, int64_t D, double lb, double ub,
+                        double Cg, double Cp, double Cw, uint64_t seed, psso_handle* out);
+
+/* Creates `count` independent swarms (1 .. 65536) that always advance
+ * together, copies their data (shift, weights, rotation) to the device, and
+ * enqueues generation 0 for all of them.  cfg may be NULL (defaults).  All
+ * instances must share one lattice. */
+psso_status psso_create_ex(const psso_problem* problems, int32_t count,
+                           const psso_config* cfg, psso_handle* out);
+
+/* Enqueues `generations` (>= 0) further SSO generations (Alg. 2) for every
+ * instance as one persistent cooperative launch. */
+psso_status psso_run(psso_handle h, int64_t generations);
+
+/* Waits for the handle's stream and reports any device-side failure. */
+psso_status psso_sync(psso_handle h);
+
+/* gBest of instance `instance` after the last completed generation: FP64
+ * fitness (`value`), particle index, and the D-value row (`row`, may be NULL).
+ * In F32_RECHECK mode the FP64 value is computed on demand.  Synchronises. */
+psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* index,
+                      double* row);
+
+/* Copies positions X (N*D), pBests P (N*D) and pBest fitness pF (N) of one
+ * instance to the host (FP64 values; any pointer may be NULL).  In
+ * F32_RECHECK mode pF holds the FP64 value where known, else the midpoint of
+ * the FP32 bounds.  Synchronises. */
+psso_status psso_get_state(psso_handle h, int32_t instance, double* X, double* P, double* pF);
+
+/* Copies up to `cap` of instance `instance`'s log entries (oldest first) and
+ * sets *n to the number copied.  Synchronises. */
+psso_status psso_get_log(psso_handle h, int32_t instance, psso_log_entry* buf, int64_t cap,
+                         int64_t* n);
+
+/* Counters since creation.  Does not synchronise. */
+psso_status psso_stats(psso_handle h, psso_stats_t* out);
+
+/* Generation number of the last enqueued generation (0 after create). */
+int64_t psso_generation(psso_handle h);
+
+/* Serialises the full state (positions, pBests, fitness, gBest, generation,
+ * counters) into `buf` (host, `cap` bytes); *n receives the size needed.  With
+ * buf == NULL only *n is set.  Runs resumed from a saved state are
+ * bit-identical to uninterrupted runs.  Synchronises. */
+psso_status psso_save(psso_handle h, void* buf, size_t cap, size_t* n);
+
+/* Restores a state written by psso_save for a handle created with the same
+ * problems and configuration. */
+psso_status psso_load(psso_handle h, const void* buf, size_t n);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* psso_last_error(void);
+
+/* Frees the handle and its device memory.  NULL is ignored. */
+void psso_destroy(psso_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSSO_H */

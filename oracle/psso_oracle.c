@@ -121,8 +121,23 @@ uint32_t oracle_rho(uint64_t seed, uint32_t sid, uint32_t g, uint32_t i, uint32_
  *   FP64 lattice: 53 random bits from words (2(j&1), 2(j&1)+1) of the block at
  *                 counter j>>1; u = m 2^-53; x = fma(ub-lb, u, lb), clamped.
  *   FP32 lattice: 24 random bits from word j&3 of the block at counter j>>2;
- *                 u = m 2^-24; y = fma(ub-lb, u, lb) in FP64; x = nearest
- *                 float to y, moved one float step inward if it left [lb,ub]. */
+ *                 u = m 2^-24 (a float); x = fmaf(S, u, L) with S, L the
+ *                 nearest floats to ub-lb and lb; x is then clamped to
+ *                 [lbf, ubf], the smallest / largest floats inside [lb, ub]. */
+static float float_at_or_above(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+static float float_at_or_below(double v)
+{
+    float f = (float)v;
+    if ((double)f > v) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
 double oracle_fresh(int lattice, uint64_t seed, uint32_t sid, uint32_t tag, uint32_t g,
                     uint32_t i, uint32_t j, double lb, double ub)
 {
@@ -138,12 +153,12 @@ double oracle_fresh(int lattice, uint64_t seed, uint32_t sid, uint32_t tag, uint
         return x;
     } else {
         philox_block(seed, j >> 2, i, g, tag, sid, w);
-        uint32_t m = w[j & 3] >> 8;
-        double u = ldexp((double)m, -24);
-        double y = fma(ub - lb, u, lb);
-        float x = (float)y;
-        if ((double)x < lb) x = nextafterf(x, INFINITY);
-        if ((double)x > ub) x = nextafterf(x, -INFINITY);
+        float u = ldexpf((float)(w[j & 3] >> 8), -24);
+        float S = (float)(ub - lb), L = (float)lb;
+        float x = fmaf(S, u, L);
+        float lbf = float_at_or_above(lb), ubf = float_at_or_below(ub);
+        if (x < lbf) x = lbf;
+        if (x > ubf) x = ubf;
         return (double)x;
     }
 }
@@ -319,6 +334,7 @@ int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
     if (fn < 0 || fn >= FN_COUNT || N < 1 || D < 1 || t < 0) return -1;
     if (!(lb < ub) || !(0.0 <= Cg && Cg <= Cp && Cp <= Cw && Cw <= 1.0)) return -2;
     if (lattice != LATTICE_F64 && lattice != LATTICE_F32) return -3;
+    if (lattice == LATTICE_F32 && !(float_at_or_above(lb) <= float_at_or_below(ub))) return -2;
     if ((fn == FN_ELLIPSOID || fn == FN_ROT_ELLIPSOID) && !w) return -4;
     if ((fn == FN_ROT_ELLIPSOID || fn == FN_ROT_RASTRIGIN || fn == FN_ROT_ACKLEY) && !M) return -4;
     if (N > 0xffffffffLL || D > 0xffffffffLL || t > 0xffffffffLL || sid >= (1u << 24)) return -5;

@@ -4,6 +4,7 @@ The reference is Triton's own Philox-4x32-10 (``tl.philox``), run on the CPU by
 Triton's interpreter in a child process: an implementation written by other
 people from the same published definition (Salmon et al., SC'11)."""
 import json
+from fractions import Fraction
 import os
 import subprocess
 import sys
@@ -110,11 +111,31 @@ def test_fresh_lattice_maps_triton_words():
         got64 = oracle.fresh("f64", seed, sid, oracle.TAG_FRESH, g, i, j, lb, ub)
         assert abs(got64 - expect64) <= 2 * np.spacing(ub)
         m32 = b[j & 3] >> 8
-        y = (ub - lb) * (m32 / 2.0**24) + lb
+        S, L = np.float32(ub - lb), np.float32(lb)
+        expect32 = _rn32(Fraction(float(S)) * Fraction(m32, 2**24) + Fraction(float(L)))
+        expect32 = min(max(expect32, _float_ge(lb)), _float_le(ub))
         got32 = oracle.fresh("f32", seed, sid, oracle.TAG_FRESH, g, i, j, lb, ub)
-        assert got32 == float(np.float32(got32))          # on the float lattice
-        assert abs(got32 - y) <= float(np.spacing(np.float32(abs(y)))) + 1e-15
+        assert got32 == expect32
         assert lb <= got32 <= ub
+
+
+def _rn32(fr):
+    """Nearest float32 (ties to even) to the exact rational fr."""
+    f = np.float32(float(fr))
+    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+    best = min(cands, key=lambda c: (abs(Fraction(float(c)) - fr),
+                                     int(np.array(c, dtype=np.float32).view(np.uint32)) & 1))
+    return float(best)
+
+
+def _float_ge(v):
+    f = np.float32(v)
+    return float(np.nextafter(f, np.float32(np.inf)) if float(f) < v else f)
+
+
+def _float_le(v):
+    f = np.float32(v)
+    return float(np.nextafter(f, np.float32(-np.inf)) if float(f) > v else f)
 
 
 def test_fresh_exact_unit_interval():
