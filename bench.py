@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the SSO hot path on GB300 (one JSON line on stdout).
+
+A step is one complete SSO run of the workload -- the initial population and
+t generations, each generation = Eq. 2.1 update of every variable + fitness
+of every particle + pBest update + gBest arg-min -- through the C ABI.
+
+Default workload: shifted Rastrigin, D=100, N=1024, t=5000, bounds
+[-5.12, 5.12], o ~ U[-4,4]^D, FP32 lattice, FP32 fitness with FP64 recheck;
+the FP64-fitness path on the same workload is timed beside it.
+
+  value   particle-variable updates / s (N*D*t per step), device-timed with
+          CUDA events on the library's stream, state resident in HBM; L2 is
+          flushed (256 MiB write) between steps, outside the timed steps
+  e2e     the same metric through the public API with host buffers: create
+          (problem data host->device), run, best (result device->host),
+          destroy, wall-clock with a device sync on both sides
+  roofline  the persistent generation kernel against the ALU issue peak
+  cpu_baseline  the CPU oracle on the host cores, bounded sample
+
+Multi-GPU: replicas only (one independent swarm per rank, stream id = rank,
+no collective on the data path); value = all ranks' updates / max time.
+`--impl reference` times the CPU oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-variable updates/s"
+UNIT = "updates/s"
+SM_COUNT = 152
+LANES_PER_SM = 128            # 4 sub-partitions x 32 lanes, one warp instruction each per clock
+ALU_CLOCK_MHZ = 2070.0        # maximum SM clock of a GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rastrigin_d100")
+    ap.add_argument("--generations", type=int, default=0, help="override t (0 = the workload's)")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--threads-per-block", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def philox_blocks_per_update(p):
+    """Philox-4x32-10 blocks one update needs: one rho block per 4 variables,
+    plus the fresh-value block(s) of a 4-variable chunk when any of its 4 draws
+    selects a fresh value (probability 1 - Cw^4)."""
+    fresh_blocks = 1 if p["lattice"] == "f32" else 2
+    return 0.25 + fresh_blocks * (1.0 - p["Cw"] ** 4) / 4.0
+
+
+# 32-bit operations of one fitness term in the FP32 path (see the kernel).
+FIT32_OPS = {"sphere": 3, "ellipsoid": 4, "rastrigin": 17, "rosenbrock": 9, "ackley": 19}
+
+
+def alu_ops_per_update(p):
+    """Algorithmic 32-bit ALU operations per particle-variable update: Philox
+    (10 rounds x 8 ops), Eq. 2.1 selection (3 compares + select), the fresh-value
+    map (4 ops at rate 1 - Cw), and the FP32 fitness term."""
+    return (80.0 * philox_blocks_per_update(p) + 4.0 + 4.0 * (1.0 - p["Cw"])
+            + FIT32_OPS[p["fn"]])
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(problems, t_full, seconds):
+    """The CPU oracle (as it stands) on all host cores for a bounded sample:
+    the first t_s generations of the workload, t_s sized to ~`seconds`."""
+    import oracle
+    threads = max(1, os.cpu_count() or 1)
+    p = problems[0]
+
+    def run(t):
+        t0 = time.perf_counter()
+        oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
+                   p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
+                   M=p["M"], nthreads=threads)
+        return time.perf_counter() - t0
+
+    probe = run(2)
+    per_gen = max(probe / 3.0, 1e-6)
+    t_s = int(max(2, min(t_full, seconds / per_gen)))
+    el = run(t_s)
+    upd = p["N"] * p["D"] * t_s
+    return {"value": upd / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{p['fn']} N={p['N']} D={p['D']}: initial population + first {t_s} "
+                      f"generations in FP64, {threads} OpenMP threads, {el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workload
+    cfg = workload.config(args.workload)
+    p = cfg["problems"][0]
+    threads = max(1, os.cpu_count() or 1)
+    t_full = args.generations or cfg["t"]
+    # size one step to ~ (budget / steps) seconds of CPU work
+    budget = min(120.0, 8.0 * max(1, args.steps))
+
+    def one(t):
+        t0 = time.perf_counter()
+        oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
+                   p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
+                   M=p["M"], nthreads=threads)
+        return time.perf_counter() - t0
+
+    per_gen = max(one(2) / 3.0, 1e-6)
+    t_s = int(max(1, min(t_full, budget / max(1, args.steps) / per_gen)))
+    for _ in range(args.warmup):
+        one(1)
+    times = [one(t_s) for _ in range(args.steps)]
+    upd = p["N"] * p["D"] * t_s
+    value = upd * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": p["N"], "D": p["D"], "t": t_s,
+                       "note": "each step is a bounded sample of the workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {t_s} generations per step, {threads} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2110_01470_gb300.build import build_library
+    build_library()
+    import paper_2110_01470_gb300 as psso
+    import workload
+
+    cfg = workload.config(args.workload)
+    t = args.generations or cfg["t"]
+    problems = [dict(p, sid=rank) for p in cfg["problems"]]
+    prec = cfg["precision"]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    upd_per_step = sum(p["N"] * p["D"] for p in problems) * t
+    evals_per_step = sum(p["N"] for p in problems) * (t + 1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(h, steps, warm):
+        for _ in range(warm):
+            psso.psso_reset(h)
+            psso.psso_run(h, t)
+        psso.psso_sync(h)
+        step_ms, kern_ms = [], []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            psso.psso_reset(h)
+            e1.record(stream)
+            psso.psso_run(h, t)
+            e2.record(stream)
+            e2.synchronize()
+            step_ms.append(e0.elapsed_time(e2))
+            kern_ms.append(e1.elapsed_time(e2))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        psso.psso_sync(h)
+        return step_ms, kern_ms
+
+    # --- main arm: the workload's precision -------------------------------------------
+    h = psso.psso_create_ex(problems, prec, stream=sptr,
+                            threads_per_block=args.threads_per_block)
+    st = psso.psso_stats(h)
+    with ClockSampler(local) as clk:
+        step_ms, kern_ms = timed_steps(h, args.steps, args.warmup)
+    rechecks = psso.psso_stats(h)["rechecks"]
+    best = psso.psso_best(h, 0)
+    psso.psso_destroy(h)
+    total = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    value = upd_per_step * args.steps * world / (total / 1e3)
+    evals = evals_per_step * args.steps * world / (total / 1e3)
+
+    # --- FP64-fitness arm on the same workload ------------------------------------------
+    fp64 = None
+    if prec != "f64" and args.fp64_steps > 0:
+        h = psso.psso_create_ex(problems, "f64", stream=sptr,
+                                threads_per_block=args.threads_per_block)
+        s64, k64 = timed_steps(h, args.fp64_steps, 1)
+        b64 = psso.psso_best(h, 0)
+        psso.psso_destroy(h)
+        v64 = upd_per_step * len(s64) / (sum(s64) / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": sum(s64) / len(s64),
+                "kernel_ms": sum(k64) / len(k64), "speedup_f32_over_f64": value / world / v64,
+                "same_gbest": bool(b64[1] == best[1] and b64[0] == best[0])}
+
+    # --- end to end through the public API with host buffers ------------------------------
+    e2e_t, h2d, d2h = [], 0, 0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = psso.psso_create_ex(problems, prec, stream=sptr,
+                                threads_per_block=args.threads_per_block)
+        psso.psso_run(h, t)
+        v, i, row = psso.psso_best(h, 0, problems[0]["D"])
+        s = psso.psso_stats(h)
+        psso.psso_destroy(h)
+        torch.cuda.synchronize()
+        if k > 0:                       # the first call pays one-time module loading
+            e2e_t.append(time.perf_counter() - t0)
+            h2d, d2h = s["h2d_bytes"], s["d2h_bytes"]
+    e2e_value = upd_per_step * len(e2e_t) / sum(e2e_t) * world if e2e_t else None
+
+    # --- roofline of the persistent generation kernel ------------------------------------
+    p0 = problems[0]
+    ops = alu_ops_per_update(p0) * upd_per_step / len(problems) * len(problems)
+    kernel_s = (sum(kern_ms) / len(kern_ms)) / 1e3
+    peak = SM_COUNT * LANES_PER_SM * ALU_CLOCK_MHZ * 1e6 / 1e12     # T ops / s
+    achieved = ops / kernel_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "sso_generations<float, true>" if prec == "f32" else
+                          "sso_generations<..., false>",
+                "ops_per_update": alu_ops_per_update(p0),
+                "kernel_ms_per_launch": kernel_s * 1e3,
+                "peak_note": "152 SMs x 128 lanes x 2070 MHz (derived, not measured)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "f32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "fn": p0["fn"], "N": p0["N"], "D": p0["D"],
+                   "t": t, "precision": "f32+f64 recheck" if prec == "f32" else "f64",
+                   "lattice": p0["lattice"], "instances_per_gpu": len(problems),
+                   "blocks": st["blocks"], "threads_per_block": st["threads_per_block"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MiB write outside the timed steps)"},
+        "fitness_evals_per_s": evals,
+        "gpu_launches": 2 * args.steps,
+        "rechecks_last_step": rechecks,
+        "gbest": {"value": best[0], "index": best[1]},
+        "fp64": fp64,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+    if world == 1 or rank == 0:
+        line["cpu_baseline"] = cpu_baseline(problems, t, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

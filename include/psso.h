@@ -118,7 +118,7 @@ typedef struct {
 /* Launch and bookkeeping options; zero-initialise for the defaults. */
 typedef struct {
     int32_t precision;          /* psso_precision                                   */
-    int32_t threads_per_block;  /* 0 = 256; a multiple of 32 in [64, 1024]          */
+    int32_t threads_per_block;  /* 0 = 256; a multiple of 32 in [64, 512]           */
     int32_t single_block_max;   /* 0 = auto: swarms of at most this many particle
                                    passes run in one block with no cross-block
                                    exchange; -1 = never                            */
@@ -131,6 +131,9 @@ typedef struct {
     int32_t fault_skip_rank;    /* testing only: 0 = off; k > 0 makes block rank k-1
                                    of instance 0 never publish, so its peers' waits
                                    run out and psso_run reports PSSO_ERR_TIMEOUT     */
+    int32_t residency;          /* 0 = auto (particle state in shared memory when it
+                                   fits), 2 = always stream it from global memory   */
+    int32_t reserved;           /* must be 0                                        */
 } psso_config;
 
 /* One log entry (psso_get_log). */
@@ -151,6 +154,8 @@ typedef struct {
     int64_t evaluations;     /* fitness evaluations, all instances                  */
     int64_t updates;         /* particle-variable updates, all instances            */
     int64_t rechecks;        /* FP64 re-evaluations (F32_RECHECK)                   */
+    int64_t h2d_bytes;       /* bytes this handle copied host -> device             */
+    int64_t d2h_bytes;       /* bytes this handle copied device -> host             */
     int32_t blocks;          /* blocks of the persistent launch                     */
     int32_t threads_per_block;
     int32_t instances;
@@ -175,6 +180,13 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count,
 /* Enqueues `generations` (>= 0) further SSO generations (Alg. 2) for every
  * instance as one persistent cooperative launch. */
 psso_status psso_run(psso_handle h, int64_t generations);
+
+/* Restarts every instance at generation 0 with the same seeds and data:
+ * clears the exchange records, gBest state and log, and enqueues the initial
+ * population again (Kernel Function (I), Sec. 2.3.1).  No allocation; also
+ * clears a failed state.  The run that follows is identical to one on a new
+ * handle. */
+psso_status psso_reset(psso_handle h);
 
 /* Waits for the handle's stream and reports any device-side failure. */
 psso_status psso_sync(psso_handle h);
@@ -211,6 +223,17 @@ psso_status psso_save(psso_handle h, void* buf, size_t cap, size_t* n);
 /* Restores a state written by psso_save for a handle created with the same
  * problems and configuration. */
 psso_status psso_load(psso_handle h, const void* buf, size_t n);
+
+/* Batched fitness (Kernel Function (E), Sec. 2.3.2): f_i = f(X_i) for N rows of
+ * D values.  X (N*D, row-major), shift/weights/rotation as in psso_problem and
+ * the outputs are host pointers.  precision = PSSO_PREC_F64 gives the FP64
+ * value in the library's fixed summation order (bit-identical to the oracle);
+ * PSSO_PREC_F32_RECHECK gives the FP32 value and, in err (may be NULL), its
+ * rigorous bound |f32 - f64| <= err; it needs every X and shift value to be a
+ * float.  stream: cudaStream_t or NULL.  Synchronises. */
+psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const double* X, const double* shift,
+                          const double* weights, const double* rotation, int32_t precision,
+                          double* f, double* err, void* stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);

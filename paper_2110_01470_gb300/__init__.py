@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) implementation of the hot path of Parallel Simplified Swarm
+Optimization (Yeh, Liu, Tan, Huang, arXiv 2110.01470).
+
+This module is a thin ctypes binding over the C ABI of ``include/psso.h``:
+the same entry points, with argument marshalling only.  Every step of an SSO
+generation (Eq. 2.1 update, fitness, pBest update, gBest arg-min) runs in the
+CUDA kernels of ``libpsso.so``; there is no CPU fallback -- importing works
+without a GPU, but any call fails loudly if the library is missing.
+
+    import paper_2110_01470_gb300 as psso
+    h = psso.psso_create(psso.PSSO_SPHERE, 100, 30, -100, 100, 0.4, 0.7, 0.9, 1)
+    psso.psso_run(h, 1000)
+    value, index, row = psso.psso_best(h, 0)
+    psso.psso_destroy(h)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsso.so")
+
+# psso_status
+PSSO_OK, PSSO_ERR_ARG, PSSO_ERR_CUDA, PSSO_ERR_OOM, PSSO_ERR_TIMEOUT, PSSO_ERR_STATE, \
+    PSSO_ERR_UNSUPPORTED = range(7)
+# psso_fn
+PSSO_SPHERE, PSSO_ELLIPSOID, PSSO_RASTRIGIN, PSSO_ROSENBROCK, PSSO_ACKLEY, \
+    PSSO_ROT_ELLIPSOID, PSSO_ROT_RASTRIGIN, PSSO_ROT_ACKLEY = range(8)
+PSSO_LATTICE_F64, PSSO_LATTICE_F32 = 0, 1
+PSSO_PREC_F64, PSSO_PREC_F32_RECHECK = 0, 1
+
+FN = {"sphere": PSSO_SPHERE, "ellipsoid": PSSO_ELLIPSOID, "rastrigin": PSSO_RASTRIGIN,
+      "rosenbrock": PSSO_ROSENBROCK, "ackley": PSSO_ACKLEY, "rot_ellipsoid": PSSO_ROT_ELLIPSOID,
+      "rot_rastrigin": PSSO_ROT_RASTRIGIN, "rot_ackley": PSSO_ROT_ACKLEY}
+LATTICE = {"f64": PSSO_LATTICE_F64, "f32": PSSO_LATTICE_F32}
+PRECISION = {"f64": PSSO_PREC_F64, "f32": PSSO_PREC_F32_RECHECK}
+
+_STATUS_NAMES = {0: "PSSO_OK", 1: "PSSO_ERR_ARG", 2: "PSSO_ERR_CUDA", 3: "PSSO_ERR_OOM",
+                 4: "PSSO_ERR_TIMEOUT", 5: "PSSO_ERR_STATE", 6: "PSSO_ERR_UNSUPPORTED"}
+
+
+class PssoError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class psso_problem(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_int32), ("lattice", ctypes.c_int32), ("N", ctypes.c_int64),
+                ("D", ctypes.c_int64), ("lb", ctypes.c_double), ("ub", ctypes.c_double),
+                ("Cg", ctypes.c_double), ("Cp", ctypes.c_double), ("Cw", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("shift", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("rotation", ctypes.c_void_p)]
+
+
+class psso_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("single_block_max", ctypes.c_int32), ("log_stride", ctypes.c_int32),
+                ("log_capacity", ctypes.c_int64), ("spin_limit", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("max_blocks", ctypes.c_int32),
+                ("fault_skip_rank", ctypes.c_int32), ("residency", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class psso_log_entry(ctypes.Structure):
+    _fields_ = [("generation", ctypes.c_int64), ("index", ctypes.c_int64),
+                ("value", ctypes.c_double), ("value_lo", ctypes.c_float),
+                ("value_hi", ctypes.c_float), ("accepted", ctypes.c_int64),
+                ("rechecks", ctypes.c_int64)]
+
+
+class psso_stats_t(ctypes.Structure):
+    _fields_ = [("generations", ctypes.c_int64), ("evaluations", ctypes.c_int64),
+                ("updates", ctypes.c_int64), ("rechecks", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
+                ("blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("instances", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpsso.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2110_01470_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    st = ctypes.c_int
+    sig = {
+        "psso_create": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_uint64, ctypes.POINTER(H)], st),
+        "psso_create_ex": ([ctypes.POINTER(psso_problem), ctypes.c_int32,
+                            ctypes.POINTER(psso_config), ctypes.POINTER(H)], st),
+        "psso_run": ([H, ctypes.c_int64], st),
+        "psso_sync": ([H], st),
+        "psso_reset": ([H], st),
+        "psso_best": ([H, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p], st),
+        "psso_get_state": ([H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p], st),
+        "psso_get_log": ([H, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                          ctypes.POINTER(ctypes.c_int64)], st),
+        "psso_stats": ([H, ctypes.POINTER(psso_stats_t)], st),
+        "psso_generation": ([H], ctypes.c_int64),
+        "psso_save": ([H, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)], st),
+        "psso_load": ([H, ctypes.c_void_p, ctypes.c_size_t], st),
+        "psso_evaluate": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_last_error": ([], ctypes.c_char_p),
+        "psso_destroy": ([H], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != PSSO_OK:
+        raise PssoError(status, load().psso_last_error().decode())
+
+
+def _f64(a, n):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# --- the C ABI, one function each ------------------------------------------------
+def psso_create(fn, N, D, lb, ub, Cg, Cp, Cw, seed):
+    h = ctypes.c_void_p()
+    _check(load().psso_create(int(fn), N, D, lb, ub, Cg, Cp, Cw, seed, ctypes.byref(h)))
+    return h
+
+
+def psso_create_ex(problems, precision=PSSO_PREC_F64, *, threads_per_block=0,
+                   single_block_max=0, log_stride=0, log_capacity=0, spin_limit=0, stream=None,
+                   max_blocks=0, fault_skip_rank=0, residency=0):
+    """``problems``: list of dicts with keys fn, N, D, lb, ub, Cg, Cp, Cw, seed and
+    optional lattice, sid / stream_id, o / shift, w / weights, M / rotation."""
+    arr = (psso_problem * len(problems))()
+    keep = []
+    for k, p in enumerate(problems):
+        D = int(p["D"])
+        o = _f64(p.get("o", p.get("shift")), D)
+        w = _f64(p.get("w", p.get("weights")), D)
+        M = _f64(p.get("M", p.get("rotation")), D * D)
+        keep += [o, w, M]
+        fn = p["fn"]
+        lat = p.get("lattice", PSSO_LATTICE_F64)
+        arr[k] = psso_problem(FN[fn] if isinstance(fn, str) else int(fn),
+                              LATTICE[lat] if isinstance(lat, str) else int(lat),
+                              int(p["N"]), D, float(p["lb"]), float(p["ub"]), float(p["Cg"]),
+                              float(p["Cp"]), float(p["Cw"]), int(p["seed"]),
+                              int(p.get("sid", p.get("stream_id", 0))), 0, _ptr(o), _ptr(w),
+                              _ptr(M))
+    if isinstance(precision, str):
+        precision = PRECISION[precision]
+    cfg = psso_config(int(precision), threads_per_block, single_block_max, log_stride,
+                      log_capacity, spin_limit, stream, max_blocks, fault_skip_rank, residency, 0)
+    h = ctypes.c_void_p()
+    _check(load().psso_create_ex(arr, len(problems), ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def psso_run(h, generations):
+    _check(load().psso_run(h, int(generations)))
+
+
+def psso_reset(h):
+    _check(load().psso_reset(h))
+
+
+def psso_sync(h):
+    _check(load().psso_sync(h))
+
+
+def psso_best(h, instance=0, D=None):
+    """Returns (value, index, row); row has D values when D is given."""
+    v = ctypes.c_double()
+    i = ctypes.c_int64()
+    row = None if D is None else np.empty(int(D), dtype=np.float64)
+    _check(load().psso_best(h, instance, ctypes.byref(v), ctypes.byref(i), _ptr(row)))
+    return v.value, i.value, row
+
+
+def psso_get_state(h, instance, N, D):
+    X = np.empty((N, D), dtype=np.float64)
+    P = np.empty((N, D), dtype=np.float64)
+    pF = np.empty(N, dtype=np.float64)
+    _check(load().psso_get_state(h, instance, _ptr(X), _ptr(P), _ptr(pF)))
+    return X, P, pF
+
+
+def psso_get_log(h, instance=0, cap=1 << 20):
+    n = ctypes.c_int64()
+    _check(load().psso_get_log(h, instance, None, 0, ctypes.byref(n)))
+    m = min(cap, n.value)
+    buf = (psso_log_entry * max(1, m))()
+    _check(load().psso_get_log(h, instance, ctypes.addressof(buf), m, ctypes.byref(n)))
+    out = {k: np.empty(n.value, dtype=dt) for k, dt in
+           (("generation", np.int64), ("index", np.int64), ("value", np.float64),
+            ("value_lo", np.float32), ("value_hi", np.float32), ("accepted", np.int64),
+            ("rechecks", np.int64))}
+    for q in range(n.value):
+        for k in out:
+            out[k][q] = getattr(buf[q], k)
+    return out
+
+
+def psso_stats(h):
+    s = psso_stats_t()
+    _check(load().psso_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in psso_stats_t._fields_ if k != "reserved"}
+
+
+def psso_generation(h):
+    return int(load().psso_generation(h))
+
+
+def psso_save(h):
+    n = ctypes.c_size_t()
+    _check(load().psso_save(h, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().psso_save(h, buf, n.value, ctypes.byref(n)))
+    return buf.raw
+
+
+def psso_load(h, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check(load().psso_load(h, buf, len(data)))
+
+
+def psso_evaluate(fn, X, shift=None, weights=None, rotation=None, precision=PSSO_PREC_F64,
+                  stream=None):
+    """Batched fitness of the rows of X (N x D).  Returns (f, err)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[None, :]
+    N, D = X.shape
+    o = _f64(shift, D)
+    w = _f64(weights, D)
+    M = _f64(rotation, D * D)
+    if isinstance(fn, str):
+        fn = FN[fn]
+    if isinstance(precision, str):
+        precision = PRECISION[precision]
+    f = np.empty(N, dtype=np.float64)
+    e = np.empty(N, dtype=np.float64)
+    _check(load().psso_evaluate(int(fn), N, D, _ptr(X), _ptr(o), _ptr(w), _ptr(M),
+                                int(precision), _ptr(f), _ptr(e), stream))
+    return f, e
+
+
+def psso_last_error():
+    return load().psso_last_error().decode()
+
+
+def psso_destroy(h):
+    if h is not None and h.value:
+        load().psso_destroy(h)
+        h.value = None

@@ -1,0 +1,751 @@
+// psso_api.cu -- the C ABI declared in include/psso.h: argument checks, the
+// launch planner, the device arena, and the host side of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "psso.h"
+#include "psso_internal.h"
+
+using namespace psso;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+psso_status fail(psso_status st, const std::string& msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? PSSO_ERR_OOM : PSSO_ERR_CUDA,   \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pow2_ceil(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+float float_at_or_above(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+float float_at_or_below(double v)
+{
+    float f = (float)v;
+    if ((double)f > v) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+enum Variant { V_F64_LAT64 = 0, V_F64_LAT32 = 1, V_F32R = 2 };
+
+struct HostInst {
+    psso_problem pr;
+    std::vector<double> o, w;
+    int G = 0, maxc = 0, nchunks = 0, Dp = 0, R = 1;
+    size_t off_X = 0, off_P = 0, off_pf64 = 0, off_plo = 0, off_phi = 0, off_pver = 0,
+           off_pflag = 0, off_grow = 0, off_rec = 0, off_rec2 = 0, off_gb = 0, off_gbrow = 0,
+           off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0;
+};
+
+}  // namespace
+
+void psso::set_last_error(const char* msg) { g_last_error = msg; }
+
+struct psso_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    psso_config cfg{};
+    int precision = PSSO_PREC_F64;
+    int lattice = PSSO_LATTICE_F64;
+    int variant = V_F64_LAT64;
+    size_t pos_size = 8;
+    std::vector<HostInst> inst;
+    std::vector<UnitDev> units;
+    std::vector<int32_t> block_first;
+    int grid = 0, block = 256;
+    size_t smem = 0;
+    char* arena = nullptr;
+    size_t arena_size = 0, state_off = 0;
+    size_t off_instdev = 0, off_units = 0, off_block_first = 0, off_status = 0;
+    int64_t gen = 0;
+    int64_t evals = 0, updates = 0;
+    int64_t h2d = 0, d2h = 0;
+    bool failed = false;
+};
+
+namespace {
+
+cudaError_t launch_variant(int v, const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    switch (v) {
+    case V_F64_LAT64: return launch_gen_f64_lat64(p, grid, block, smem, s);
+    case V_F64_LAT32: return launch_gen_f64_lat32(p, grid, block, smem, s);
+    default: return launch_gen_f32r(p, grid, block, smem, s);
+    }
+}
+
+psso_status check_problem(const psso_problem& pr, int precision, int idx)
+{
+    const std::string at = "problem " + std::to_string(idx) + ": ";
+    if (pr.fn < PSSO_SPHERE || pr.fn > PSSO_ROT_ACKLEY) return fail(PSSO_ERR_ARG, at + "unknown function id");
+    if (pr.fn >= PSSO_ROT_ELLIPSOID)
+        return fail(PSSO_ERR_UNSUPPORTED, at + "rotated functions are not available in this build");
+    if (pr.N < 1 || pr.N > 0x7fffffffLL) return fail(PSSO_ERR_ARG, at + "N must be in [1, 2^31-1]");
+    if (pr.D < 1 || pr.D > 32 * MAX_CHUNKS_PER_LANE * 4) return fail(PSSO_ERR_ARG, at + "D must be in [1, 1024]");
+    if (!std::isfinite(pr.lb) || !std::isfinite(pr.ub) || !(pr.lb < pr.ub))
+        return fail(PSSO_ERR_ARG, at + "bounds must be finite with lb < ub");
+    if (!(0.0 <= pr.Cg && pr.Cg <= pr.Cp && pr.Cp <= pr.Cw && pr.Cw <= 1.0))
+        return fail(PSSO_ERR_ARG, at + "need 0 <= Cg <= Cp <= Cw <= 1");
+    if (pr.lattice != PSSO_LATTICE_F64 && pr.lattice != PSSO_LATTICE_F32)
+        return fail(PSSO_ERR_ARG, at + "unknown lattice");
+    if (pr.stream_id >= (1u << 24)) return fail(PSSO_ERR_ARG, at + "stream_id must be < 2^24");
+    if (pr.reserved != 0) return fail(PSSO_ERR_ARG, at + "reserved field must be 0");
+    if ((pr.fn == PSSO_ELLIPSOID || pr.fn == PSSO_ROT_ELLIPSOID) && !pr.weights)
+        return fail(PSSO_ERR_ARG, at + "ellipsoid functions need weights");
+    if (pr.lattice == PSSO_LATTICE_F32 && !(float_at_or_above(pr.lb) <= float_at_or_below(pr.ub)))
+        return fail(PSSO_ERR_ARG, at + "no float lies inside [lb, ub]");
+    if (pr.shift)
+        for (int64_t j = 0; j < pr.D; ++j)
+            if (!std::isfinite(pr.shift[j])) return fail(PSSO_ERR_ARG, at + "shift must be finite");
+    if (precision == PSSO_PREC_F32_RECHECK) {
+        if (pr.lattice != PSSO_LATTICE_F32)
+            return fail(PSSO_ERR_ARG, at + "F32_RECHECK precision needs the F32 lattice");
+        if (pr.shift)
+            for (int64_t j = 0; j < pr.D; ++j)
+                if ((double)(float)pr.shift[j] != pr.shift[j])
+                    return fail(PSSO_ERR_ARG, at + "F32_RECHECK precision needs a float-exact shift");
+    }
+    return PSSO_OK;
+}
+
+// Picks blocks per instance and assigns units to blocks.
+psso_status plan(psso_ctx* h)
+{
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
+    const int TB = h->block;
+    const int nw = TB / 32;
+    const int sbm = h->cfg.single_block_max == 0 ? 4 : (h->cfg.single_block_max < 0 ? 0 : h->cfg.single_block_max);
+    size_t unit_smem_max = 0;
+    double total_cost = 0.0;
+    for (auto& I : h->inst) {
+        I.nchunks = (int)((I.pr.D + 3) / 4);
+        I.Dp = 4 * I.nchunks;
+        I.G = std::min(32, pow2_ceil(I.nchunks));
+        I.maxc = pow2_ceil((I.nchunks + 31) / 32);
+        unit_smem_max = std::max(unit_smem_max, align_up((size_t)I.Dp * h->pos_size, 16));
+        total_cost += (double)I.pr.N * I.Dp;
+    }
+    // Occupancy with the largest single-unit footprint.
+    int bps = 0;
+    CUDA_TRY(psso::occupancy_gen(h->variant, TB, unit_smem_max, &bps));
+    if (bps < 1) return fail(PSSO_ERR_UNSUPPORTED, "kernel does not fit on one SM with this block size");
+    int grid_max = bps * prop.multiProcessorCount;
+    if (h->cfg.max_blocks > 0) grid_max = std::min(grid_max, h->cfg.max_blocks);
+
+    for (int attempt = 0; attempt < 32; ++attempt) {
+        // Blocks per instance, proportional to its work.
+        std::vector<int> R(h->inst.size());
+        int64_t sumR = 0;
+        for (size_t k = 0; k < h->inst.size(); ++k) {
+            const HostInst& I = h->inst[k];
+            const int ppp = nw * (32 / I.G);
+            const int64_t passes = (I.pr.N + ppp - 1) / ppp;
+            int64_t r = 1;
+            if (passes > sbm) {
+                r = (int64_t)std::floor((double)grid_max * ((double)I.pr.N * I.Dp) / total_cost);
+                r = std::max<int64_t>(1, std::min<int64_t>(r, passes));
+                r = std::min<int64_t>(r, grid_max);
+            }
+            R[k] = (int)r;
+            sumR += r;
+        }
+        // Units: whole passes per block.
+        std::vector<UnitDev> units;
+        std::vector<double> cost;
+        for (size_t k = 0; k < h->inst.size(); ++k) {
+            HostInst& I = h->inst[k];
+            I.R = R[k];
+            const int ppp = nw * (32 / I.G);
+            const int64_t passes = (I.pr.N + ppp - 1) / ppp;
+            for (int r = 0; r < R[k]; ++r) {
+                UnitDev u{};
+                u.inst = (int32_t)k;
+                u.rank = r;
+                u.i0 = std::min<int64_t>(I.pr.N, (passes * r / R[k]) * ppp);
+                u.i1 = std::min<int64_t>(I.pr.N, (passes * (r + 1) / R[k]) * ppp);
+                units.push_back(u);
+                cost.push_back((double)(u.i1 - u.i0) * I.Dp + 64.0 * I.Dp);
+            }
+        }
+        // Pack units onto blocks (longest first onto the least loaded block).
+        const int nblocks = (int)std::min<int64_t>(sumR, grid_max);
+        std::vector<std::vector<int>> members(nblocks);
+        std::vector<double> load(nblocks, 0.0);
+        std::vector<int> order(units.size());
+        for (size_t q = 0; q < units.size(); ++q) order[q] = (int)q;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        bool ok = true;
+        for (int q : order) {
+            int best = -1;
+            for (int b = 0; b < nblocks; ++b)
+                if ((int)members[b].size() < MAX_UNITS_PER_BLOCK && (best < 0 || load[b] < load[best])) best = b;
+            if (best < 0) { ok = false; break; }
+            members[best].push_back(q);
+            load[best] += cost[q];
+        }
+        if (!ok) return fail(PSSO_ERR_UNSUPPORTED, "too many instances for one launch");
+        // Shared memory: every unit keeps its gBest row there; units whose X, P
+        // and pBest state also fit the per-block budget stay resident.
+        const int per_sm = std::max(1, (nblocks + prop.multiProcessorCount - 1) / prop.multiProcessorCount);
+        const size_t sm_total = (size_t)prop.sharedMemPerMultiprocessor;
+        const size_t budget = std::min<size_t>((size_t)prop.sharedMemPerBlockOptin - 8192,
+                                               sm_total / per_sm > 12288 ? sm_total / per_sm - 12288 : 0);
+        h->units.clear();
+        h->block_first.assign(1, 0);
+        size_t smem = 0;
+        for (int b = 0; b < nblocks; ++b) {
+            std::sort(members[b].begin(), members[b].end(), [&](int a, int c) {
+                return units[a].inst != units[c].inst ? units[a].inst < units[c].inst
+                                                      : units[a].rank < units[c].rank;
+            });
+            size_t off = 0;
+            for (int q : members[b]) off += align_up((size_t)h->inst[units[q].inst].Dp * h->pos_size, 16);
+            for (int q : members[b]) {
+                UnitDev u = units[q];
+                const HostInst& I = h->inst[u.inst];
+                const size_t rb = resident_bytes(u.i1 - u.i0, I.Dp, (int)h->pos_size);
+                u.resident = (h->cfg.residency != 2 && off + rb <= budget) ? 1 : 0;
+                u.res_off = u.resident ? (int32_t)off : 0;
+                if (u.resident) off += rb;
+                units[q] = u;
+            }
+            size_t goff = 0;
+            for (int q : members[b]) {
+                UnitDev u = units[q];
+                u.smem_off = (int32_t)goff;
+                goff += align_up((size_t)h->inst[u.inst].Dp * h->pos_size, 16);
+                h->units.push_back(u);
+            }
+            smem = std::max(smem, off);
+            h->block_first.push_back((int32_t)h->units.size());
+        }
+        if (smem > (size_t)prop.sharedMemPerBlockOptin - 8192)
+            return fail(PSSO_ERR_UNSUPPORTED, "per-block gBest rows exceed shared memory");
+        CUDA_TRY(psso::set_smem_gen(h->variant, smem));
+        int bps2 = 0;
+        CUDA_TRY(psso::occupancy_gen(h->variant, TB, smem, &bps2));
+        if ((int64_t)bps2 * prop.multiProcessorCount >= nblocks) {
+            h->grid = nblocks;
+            h->smem = smem;
+            return PSSO_OK;
+        }
+        grid_max = std::max(1, bps2 * prop.multiProcessorCount);
+    }
+    return fail(PSSO_ERR_UNSUPPORTED, "could not find a co-resident launch shape");
+}
+
+void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
+{
+    char* A = h->arena;
+    out.resize(h->inst.size());
+    for (size_t k = 0; k < h->inst.size(); ++k) {
+        const HostInst& I = h->inst[k];
+        InstDev d{};
+        d.fn = I.pr.fn;
+        d.D = (int32_t)I.pr.D;
+        d.Dp = I.Dp;
+        d.nchunks = I.nchunks;
+        d.G = I.G;
+        d.maxc = I.maxc;
+        d.R = I.R;
+        d.lattice = I.pr.lattice;
+        d.N = I.pr.N;
+        d.Tg = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cg, 32));
+        d.Tp = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cp, 32));
+        d.Tw = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cw, 32));
+        d.k0 = (uint32_t)I.pr.seed;
+        d.k1 = (uint32_t)(I.pr.seed >> 32);
+        d.sid = I.pr.stream_id;
+        d.lb = I.pr.lb;
+        d.ub = I.pr.ub;
+        d.span = I.pr.ub - I.pr.lb;
+        d.S32 = (float)(I.pr.ub - I.pr.lb);
+        d.L32 = (float)I.pr.lb;
+        d.lbf = float_at_or_above(I.pr.lb);
+        d.ubf = float_at_or_below(I.pr.ub);
+        d.o64 = reinterpret_cast<const double*>(A + I.off_o64);
+        d.o32 = reinterpret_cast<const float*>(A + I.off_o32);
+        d.w64 = I.w.empty() ? nullptr : reinterpret_cast<const double*>(A + I.off_w64);
+        d.w32 = I.w.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_w32);
+        d.X = A + I.off_X;
+        d.P = A + I.off_P;
+        d.pf64 = reinterpret_cast<double*>(A + I.off_pf64);
+        d.plo = reinterpret_cast<float*>(A + I.off_plo);
+        d.phi = reinterpret_cast<float*>(A + I.off_phi);
+        d.pver = reinterpret_cast<uint32_t*>(A + I.off_pver);
+        d.pflag = reinterpret_cast<uint32_t*>(A + I.off_pflag);
+        d.grow = A + I.off_grow;
+        d.rec = reinterpret_cast<uint64_t*>(A + I.off_rec);
+        d.rec2 = reinterpret_cast<uint64_t*>(A + I.off_rec2);
+        d.gb = reinterpret_cast<GBestDev*>(A + I.off_gb);
+        d.gbrow = A + I.off_gbrow;
+        d.log = reinterpret_cast<LogDev*>(A + I.off_log);
+        d.log_cap = h->cfg.log_stride > 0 ? h->cfg.log_capacity : 0;
+        d.log_stride = h->cfg.log_stride;
+        out[k] = d;
+    }
+}
+
+psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
+{
+    KParams p{};
+    p.inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
+    p.units = reinterpret_cast<const UnitDev*>(h->arena + h->off_units);
+    p.block_first = reinterpret_cast<const int32_t*>(h->arena + h->off_block_first);
+    p.status = reinterpret_cast<StatusDev*>(h->arena + h->off_status);
+    p.g_begin = g_begin;
+    p.g_end = g_end;
+    p.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : (int64_t)50000000;
+    p.fault_skip_rank = h->cfg.fault_skip_rank;
+    CUDA_TRY(launch_variant(h->variant, p, h->grid, h->block, h->smem, h->stream));
+    return PSSO_OK;
+}
+
+psso_status read_status(psso_ctx* h)
+{
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    StatusDev st;
+    CUDA_TRY(cudaMemcpy(&st, h->arena + h->off_status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st.err != 0) {
+        h->failed = true;
+        return fail((psso_status)st.err, "a cross-block wait ran out (instance " +
+                                             std::to_string(st.where >> 16) + ", block rank " +
+                                             std::to_string(st.where & 0xffff) + ")");
+    }
+    return PSSO_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* psso_last_error(void) { return g_last_error.c_str(); }
+
+psso_status psso_create_ex(const psso_problem* problems, int32_t count, const psso_config* cfg,
+                           psso_handle* out)
+{
+    if (!out) return fail(PSSO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!problems || count < 1 || count > 65536) return fail(PSSO_ERR_ARG, "need 1..65536 problems");
+    psso_config c{};
+    if (cfg) c = *cfg;
+    if (c.precision != PSSO_PREC_F64 && c.precision != PSSO_PREC_F32_RECHECK)
+        return fail(PSSO_ERR_ARG, "unknown precision");
+    if (c.threads_per_block == 0) c.threads_per_block = 256;
+    if (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32)
+        return fail(PSSO_ERR_ARG, "threads_per_block must be a multiple of 32 in [64, 512]");
+    if (c.log_stride < 0 || c.log_capacity < 0) return fail(PSSO_ERR_ARG, "negative log settings");
+    if (c.log_stride > 0 && c.log_capacity == 0) return fail(PSSO_ERR_ARG, "log_capacity must be > 0");
+    if (c.fault_skip_rank < 0) return fail(PSSO_ERR_ARG, "fault_skip_rank must be >= 0");
+    if (c.residency != 0 && c.residency != 2) return fail(PSSO_ERR_ARG, "residency must be 0 or 2");
+    if (c.reserved != 0) return fail(PSSO_ERR_ARG, "reserved config field must be 0");
+    for (int32_t k = 0; k < count; ++k) {
+        psso_status st = check_problem(problems[k], c.precision, k);
+        if (st != PSSO_OK) return st;
+        if (problems[k].lattice != problems[0].lattice)
+            return fail(PSSO_ERR_ARG, "all problems must share one lattice");
+    }
+
+    psso_ctx* h = new psso_ctx();
+    h->cfg = c;
+    h->precision = c.precision;
+    h->lattice = problems[0].lattice;
+    h->variant = c.precision == PSSO_PREC_F32_RECHECK ? V_F32R
+                 : (h->lattice == PSSO_LATTICE_F32 ? V_F64_LAT32 : V_F64_LAT64);
+    h->pos_size = h->lattice == PSSO_LATTICE_F32 ? 4 : 8;
+    h->block = c.threads_per_block;
+    h->stream = static_cast<cudaStream_t>(c.stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(PSSO_ERR_CUDA, "no CUDA device");
+    }
+    h->inst.resize(count);
+    for (int32_t k = 0; k < count; ++k) {
+        HostInst& I = h->inst[k];
+        I.pr = problems[k];
+        I.o.assign((size_t)I.pr.D, 0.0);
+        if (I.pr.shift) std::copy(I.pr.shift, I.pr.shift + I.pr.D, I.o.begin());
+        if (I.pr.weights) I.w.assign(I.pr.weights, I.pr.weights + I.pr.D);
+        I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
+    }
+    psso_status st = plan(h);
+    if (st != PSSO_OK) {
+        delete h;
+        return st;
+    }
+
+    // Arena: descriptors first, then per-instance state (saved by psso_save).
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = align_up(off, 256);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    h->off_instdev = take(sizeof(InstDev) * h->inst.size());
+    h->off_units = take(sizeof(UnitDev) * h->units.size());
+    h->off_block_first = take(sizeof(int32_t) * h->block_first.size());
+    h->off_status = take(sizeof(StatusDev));
+    h->state_off = align_up(off, 256);
+    const bool f32r = h->precision == PSSO_PREC_F32_RECHECK;
+    const size_t logcap = c.log_stride > 0 ? (size_t)c.log_capacity : 0;
+    for (auto& I : h->inst) {
+        const size_t N = (size_t)I.pr.N, row = (size_t)I.Dp * h->pos_size;
+        I.off_X = take(N * row);
+        I.off_P = take(N * row);
+        I.off_pf64 = take(N * 8);
+        I.off_plo = take(f32r ? N * 4 : 0);
+        I.off_phi = take(f32r ? N * 4 : 0);
+        I.off_pver = take(N * 4);
+        I.off_pflag = take(f32r ? N * 4 : 0);
+        I.off_grow = take(2 * (size_t)I.R * I.Dp * (h->pos_size / 4) * 8);   // tagged words
+        I.off_rec = take(2 * (size_t)I.R * REC_WORDS * 8);
+        I.off_rec2 = take(2 * (size_t)I.R * REC_WORDS * 8);
+        I.off_gb = take(sizeof(GBestDev));
+        I.off_gbrow = take(row);
+        I.off_log = take(logcap * sizeof(LogDev));
+        I.off_o64 = take((size_t)I.Dp * 8);
+        I.off_o32 = take((size_t)I.Dp * 4);
+        I.off_w64 = take(I.w.empty() ? 0 : (size_t)I.Dp * 8);
+        I.off_w32 = take(I.w.empty() ? 0 : (size_t)I.Dp * 4);
+    }
+    h->arena_size = align_up(off, 256);
+    cudaError_t e = cudaMalloc(&h->arena, h->arena_size);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(PSSO_ERR_OOM, std::string("cudaMalloc of the state arena: ") + cudaGetErrorString(e));
+    }
+    auto cleanup_fail = [&](psso_status s2) {
+        psso_destroy(h);
+        return s2;
+    };
+    // Zero the arena, mark records / log as empty, then upload descriptors and data.
+    std::vector<InstDev> instdev;
+    fill_instdev(h, instdev);
+    const size_t desc = h->state_off;
+    std::vector<char> host(desc, 0);
+    std::memcpy(host.data() + h->off_instdev, instdev.data(), sizeof(InstDev) * instdev.size());
+    std::memcpy(host.data() + h->off_units, h->units.data(), sizeof(UnitDev) * h->units.size());
+    std::memcpy(host.data() + h->off_block_first, h->block_first.data(),
+                sizeof(int32_t) * h->block_first.size());
+    e = cudaMemsetAsync(h->arena, 0, h->arena_size, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena, host.data(), desc, cudaMemcpyHostToDevice, h->stream);
+    h->h2d += (int64_t)desc;
+    std::vector<std::vector<char>> staging;   // kept alive until the stream sync below
+    for (auto& I : h->inst) {
+        if (e != cudaSuccess) break;
+        const size_t rb = 2 * (size_t)I.R * REC_WORDS * 8;
+        e = cudaMemsetAsync(h->arena + I.off_rec, 0xff, rb, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->arena + I.off_rec2, 0xff, rb, h->stream);
+        if (e == cudaSuccess && logcap)
+            e = cudaMemsetAsync(h->arena + I.off_log, 0xff, logcap * sizeof(LogDev), h->stream);
+        const size_t nd = (size_t)I.pr.D;
+        const bool hw = !I.w.empty();
+        staging.emplace_back(nd * (hw ? 24 : 12));
+        char* b = staging.back().data();
+        double* o64 = reinterpret_cast<double*>(b);
+        float* o32 = reinterpret_cast<float*>(b + nd * 8);
+        for (size_t j = 0; j < nd; ++j) {
+            o64[j] = I.o[j];
+            o32[j] = (float)I.o[j];
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_o64, o64, nd * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_o32, o32, nd * 4, cudaMemcpyHostToDevice, h->stream);
+        h->h2d += (int64_t)(nd * 12);
+        if (hw) {
+            double* w64 = reinterpret_cast<double*>(b + nd * 12);
+            float* w32 = reinterpret_cast<float*>(b + nd * 20);
+            for (size_t j = 0; j < nd; ++j) {
+                w64[j] = I.w[j];
+                w32[j] = (float)I.w[j];
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_w64, w64, nd * 8, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_w32, w32, nd * 4, cudaMemcpyHostToDevice, h->stream);
+            h->h2d += (int64_t)(nd * 12);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        fail(PSSO_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+        return cleanup_fail(PSSO_ERR_CUDA);
+    }
+    st = launch(h, 0, 0);
+    if (st != PSSO_OK) return cleanup_fail(st);
+    for (auto& I : h->inst) h->evals += I.pr.N;
+    *out = h;
+    return PSSO_OK;
+}
+
+psso_status psso_create(psso_fn fn, int64_t N, int64_t D, double lb, double ub, double Cg,
+                        double Cp, double Cw, uint64_t seed, psso_handle* out)
+{
+    psso_problem pr{};
+    pr.fn = fn;
+    pr.lattice = PSSO_LATTICE_F64;
+    pr.N = N;
+    pr.D = D;
+    pr.lb = lb;
+    pr.ub = ub;
+    pr.Cg = Cg;
+    pr.Cp = Cp;
+    pr.Cw = Cw;
+    pr.seed = seed;
+    std::vector<double> w;
+    if ((fn == PSSO_ELLIPSOID || fn == PSSO_ROT_ELLIPSOID) && D >= 1 && D <= 1024) {
+        w.resize((size_t)D);
+        for (int64_t j = 0; j < D; ++j) w[j] = D == 1 ? 1.0 : std::pow(10.0, 6.0 * (double)j / (double)(D - 1));
+        pr.weights = w.data();
+    }
+    return psso_create_ex(&pr, 1, nullptr, out);
+}
+
+psso_status psso_run(psso_handle h, int64_t generations)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    if (generations < 0) return fail(PSSO_ERR_ARG, "generations must be >= 0");
+    if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier; destroy it or psso_load a state");
+    if (generations == 0) return PSSO_OK;
+    if (h->gen + generations > 0xfffffff0LL) return fail(PSSO_ERR_ARG, "generation counter would exceed 2^32");
+    CUDA_TRY(cudaSetDevice(h->device));
+    psso_status st = launch(h, h->gen + 1, h->gen + generations);
+    if (st != PSSO_OK) return st;
+    h->gen += generations;
+    for (auto& I : h->inst) {
+        h->evals += I.pr.N * generations;
+        h->updates += I.pr.N * I.pr.D * generations;
+    }
+    return PSSO_OK;
+}
+
+psso_status psso_reset(psso_handle h)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    CUDA_TRY(cudaSetDevice(h->device));
+    const size_t logcap = h->cfg.log_stride > 0 ? (size_t)h->cfg.log_capacity : 0;
+    for (const auto& I : h->inst) {
+        const size_t rb = 2 * (size_t)I.R * REC_WORDS * 8;
+        CUDA_TRY(cudaMemsetAsync(h->arena + I.off_rec, 0xff, rb, h->stream));
+        CUDA_TRY(cudaMemsetAsync(h->arena + I.off_rec2, 0xff, rb, h->stream));
+        if (logcap) CUDA_TRY(cudaMemsetAsync(h->arena + I.off_log, 0xff, logcap * sizeof(LogDev), h->stream));
+        CUDA_TRY(cudaMemsetAsync(h->arena + I.off_gb, 0, sizeof(GBestDev), h->stream));
+    }
+    CUDA_TRY(cudaMemsetAsync(h->arena + h->off_status, 0, sizeof(StatusDev), h->stream));
+    psso_status st = launch(h, 0, 0);
+    if (st != PSSO_OK) return st;
+    h->gen = 0;
+    h->failed = false;
+    h->evals = 0;
+    h->updates = 0;
+    for (const auto& I : h->inst) h->evals += I.pr.N;
+    return PSSO_OK;
+}
+
+psso_status psso_sync(psso_handle h)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    return read_status(h);
+}
+
+int64_t psso_generation(psso_handle h) { return h ? h->gen : -1; }
+
+static psso_status copy_row(psso_ctx* h, const HostInst& I, size_t off, int64_t nrows, double* dst)
+{
+    const size_t row = (size_t)I.Dp * h->pos_size;
+    std::vector<char> buf((size_t)nrows * row);
+    CUDA_TRY(cudaMemcpy(buf.data(), h->arena + off, buf.size(), cudaMemcpyDeviceToHost));
+    h->d2h += (int64_t)buf.size();
+    for (int64_t i = 0; i < nrows; ++i)
+        for (int64_t j = 0; j < I.pr.D; ++j)
+            dst[i * I.pr.D + j] = h->pos_size == 8
+                                      ? reinterpret_cast<const double*>(buf.data() + i * row)[j]
+                                      : (double)reinterpret_cast<const float*>(buf.data() + i * row)[j];
+    return PSSO_OK;
+}
+
+psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* index, double* row)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    psso_status st = read_status(h);
+    if (st != PSSO_OK) return st;
+    if (h->precision == PSSO_PREC_F32_RECHECK) {
+        CUDA_TRY(launch_best_f64(reinterpret_cast<const InstDev*>(h->arena + h->off_instdev),
+                                 (int)h->inst.size(), h->lattice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    const HostInst& I = h->inst[instance];
+    GBestDev gb;
+    CUDA_TRY(cudaMemcpy(&gb, h->arena + I.off_gb, sizeof gb, cudaMemcpyDeviceToHost));
+    h->d2h += (int64_t)sizeof gb;
+    if (value) *value = gb.f64;
+    if (index) *index = gb.idx;
+    if (row) return copy_row(h, I, I.off_gbrow, 1, row);
+    return PSSO_OK;
+}
+
+psso_status psso_get_state(psso_handle h, int32_t instance, double* X, double* P, double* pF)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    psso_status st = read_status(h);
+    if (st != PSSO_OK) return st;
+    const HostInst& I = h->inst[instance];
+    if (X && (st = copy_row(h, I, I.off_X, I.pr.N, X)) != PSSO_OK) return st;
+    if (P && (st = copy_row(h, I, I.off_P, I.pr.N, P)) != PSSO_OK) return st;
+    if (pF) {
+        const size_t N = (size_t)I.pr.N;
+        CUDA_TRY(cudaMemcpy(pF, h->arena + I.off_pf64, N * 8, cudaMemcpyDeviceToHost));
+        if (h->precision == PSSO_PREC_F32_RECHECK) {
+            std::vector<float> lo(N), hi(N);
+            std::vector<uint32_t> flag(N);
+            CUDA_TRY(cudaMemcpy(lo.data(), h->arena + I.off_plo, N * 4, cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(hi.data(), h->arena + I.off_phi, N * 4, cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(flag.data(), h->arena + I.off_pflag, N * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < N; ++i)
+                if (!(flag[i] & 1u)) pF[i] = 0.5 * ((double)lo[i] + (double)hi[i]);
+        }
+    }
+    return PSSO_OK;
+}
+
+psso_status psso_get_log(psso_handle h, int32_t instance, psso_log_entry* buf, int64_t cap, int64_t* n)
+{
+    if (!h || !n) return fail(PSSO_ERR_ARG, "handle or n is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    *n = 0;
+    psso_status st = read_status(h);
+    if (st != PSSO_OK) return st;
+    const int64_t lc = h->cfg.log_stride > 0 ? h->cfg.log_capacity : 0;
+    if (lc == 0) return PSSO_OK;
+    const HostInst& I = h->inst[instance];
+    std::vector<LogDev> all((size_t)lc);
+    CUDA_TRY(cudaMemcpy(all.data(), h->arena + I.off_log, all.size() * sizeof(LogDev), cudaMemcpyDeviceToHost));
+    std::vector<LogDev> valid;
+    for (const auto& e : all)
+        if (e.gen >= 0) valid.push_back(e);
+    std::sort(valid.begin(), valid.end(), [](const LogDev& a, const LogDev& b) { return a.gen < b.gen; });
+    const int64_t m = std::min<int64_t>(cap, (int64_t)valid.size());
+    static_assert(sizeof(LogDev) == sizeof(psso_log_entry), "log layout");
+    if (buf && m > 0) std::memcpy(buf, valid.data(), (size_t)m * sizeof(LogDev));
+    *n = buf ? m : (int64_t)valid.size();
+    return PSSO_OK;
+}
+
+psso_status psso_stats(psso_handle h, psso_stats_t* out)
+{
+    if (!h || !out) return fail(PSSO_ERR_ARG, "handle or out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->generations = h->gen;
+    out->evaluations = h->evals;
+    out->updates = h->updates;
+    out->blocks = h->grid;
+    out->threads_per_block = h->block;
+    out->instances = (int32_t)h->inst.size();
+    int64_t r = 0;
+    for (const auto& I : h->inst) {
+        GBestDev gb;
+        if (cudaMemcpy(&gb, h->arena + I.off_gb, sizeof gb, cudaMemcpyDeviceToHost) == cudaSuccess)
+            r += gb.total_rechecks;
+    }
+    out->rechecks = r;
+    out->h2d_bytes = h->h2d;
+    out->d2h_bytes = h->d2h;
+    return PSSO_OK;
+}
+
+struct SaveHeader {
+    char magic[8];
+    int64_t gen, evals, updates, state_bytes;
+    int32_t grid, block, n_inst, variant;
+};
+
+psso_status psso_save(psso_handle h, void* buf, size_t cap, size_t* n)
+{
+    if (!h || !n) return fail(PSSO_ERR_ARG, "handle or n is NULL");
+    const size_t state = h->arena_size - h->state_off;
+    *n = sizeof(SaveHeader) + state;
+    if (!buf) return PSSO_OK;
+    if (cap < *n) return fail(PSSO_ERR_ARG, "buffer too small");
+    psso_status st = read_status(h);
+    if (st != PSSO_OK) return st;
+    SaveHeader hd{};
+    std::memcpy(hd.magic, "PSSOST01", 8);
+    hd.gen = h->gen;
+    hd.evals = h->evals;
+    hd.updates = h->updates;
+    hd.state_bytes = (int64_t)state;
+    hd.grid = h->grid;
+    hd.block = h->block;
+    hd.n_inst = (int32_t)h->inst.size();
+    hd.variant = h->variant;
+    std::memcpy(buf, &hd, sizeof hd);
+    CUDA_TRY(cudaMemcpy(static_cast<char*>(buf) + sizeof hd, h->arena + h->state_off, state,
+                        cudaMemcpyDeviceToHost));
+    return PSSO_OK;
+}
+
+psso_status psso_load(psso_handle h, const void* buf, size_t n)
+{
+    if (!h || !buf) return fail(PSSO_ERR_ARG, "handle or buf is NULL");
+    if (n < sizeof(SaveHeader)) return fail(PSSO_ERR_ARG, "buffer too small");
+    SaveHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    const size_t state = h->arena_size - h->state_off;
+    if (std::memcmp(hd.magic, "PSSOST01", 8) != 0 || hd.state_bytes != (int64_t)state ||
+        n != sizeof hd + state || hd.grid != h->grid || hd.block != h->block ||
+        hd.n_inst != (int32_t)h->inst.size() || hd.variant != h->variant)
+        return fail(PSSO_ERR_ARG, "state was saved from a handle with other problems or launch shape");
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    CUDA_TRY(cudaMemcpy(h->arena + h->state_off, static_cast<const char*>(buf) + sizeof hd, state,
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(h->arena + h->off_status, 0, sizeof(StatusDev)));
+    h->gen = hd.gen;
+    h->evals = hd.evals;
+    h->updates = hd.updates;
+    h->failed = false;
+    return PSSO_OK;
+}
+
+void psso_destroy(psso_handle h)
+{
+    if (!h) return;
+    if (h->arena) {
+        cudaSetDevice(h->device);
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->arena);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,473 @@
+// sso_common.cuh -- device building blocks of the SSO generation kernel:
+// chunk loads/stores, fresh values, FP64 / FP32 fitness, block reductions.
+//
+// The generation kernel (sso_kernel.cuh) is summarised here for context.
+//
+// One cooperative launch runs generations g_begin..g_end of every instance.
+// Each block owns one or more "units" (a contiguous particle range of one
+// instance) for the whole launch.  Per generation and unit:
+//
+//   A  gBest of generation g-1 (Alg. 4).  A unit that is the whole swarm keeps
+//      it in shared memory.  Otherwise every block of the instance reads the
+//      per-block records of g-1 (each 64-bit word tagged with the generation, so
+//      no lock or atomic is needed), takes the lowest-index arg-min, and copies
+//      the winning row from the winner's double-buffered snapshot only if the
+//      winner (index, row version) changed.
+//   B  For every owned particle (a group of G lanes; lane l owns variable
+//      chunks l, l+32, ... of 4 variables): the stepwise update of Eq. 2.1 with
+//      a Philox-4x32-10 block per chunk, the fitness (Kernel Function (E)), and
+//      the pBest update of Alg. 3 (f <= pF).  In FP32 mode every comparison the
+//      FP32 error bound cannot decide is re-evaluated in FP64 in the oracle's
+//      order.
+//   C  The unit's lowest-index arg-min of pBest fitness.
+//   D  Whole-swarm unit: update the shared gBest row.  Otherwise publish the
+//      unit's winner row (double-buffered by generation parity) and record.
+//
+// The only coupling between blocks is the per-generation record exchange of
+// step A/D: the paper's pBest / gBest "resource preemption" (abstract,
+// Alg. 3-4) cannot occur because every block writes only its own slots.
+#pragma once
+#include <algorithm>
+#include <cfloat>
+#include <cstdint>
+
+#include "devmath.cuh"
+#include "psso_internal.h"
+
+namespace psso {
+
+constexpr float U32 = 0x1p-24f;
+
+// ---------------------------------------------------------------------------
+// Vector loads / stores of one chunk (4 positions, 16 or 32 bytes).
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4])
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4])
+{
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4_cg(const float* p, float (&v)[4])
+{
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4_cg(const double* p, double (&v)[4])
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4])
+{
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p)
+{
+    uint64_t v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v)
+{
+    asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// ---------------------------------------------------------------------------
+// Fresh values (last branch of Eq. 2.1; the initial population).
+__device__ __forceinline__ float fresh_f32(uint32_t w, const InstDev& in)
+{
+    const float u = __fmul_rn((float)(w >> 8), 0x1p-24f);
+    float x = __fmaf_rn(in.S32, u, in.L32);
+    x = (x < in.lbf) ? in.lbf : x;
+    x = (x > in.ubf) ? in.ubf : x;
+    return x;
+}
+__device__ __forceinline__ double fresh_f64(uint32_t lo, uint32_t hi, const InstDev& in)
+{
+    const uint64_t m = ((((uint64_t)hi) << 32) | lo) >> 11;
+    const double u = __dmul_rn(__ull2double_rn(m), 0x1p-53);
+    double x = __fma_rn(in.span, u, in.lb);
+    x = (x < in.lb) ? in.lb : x;
+    x = (x > in.ub) ? in.ub : x;
+    return x;
+}
+
+// Fresh values for the chunk's variables selected by `mask` (bit m = variable 4c+m).
+__device__ __forceinline__ void fresh_chunk(float (&v)[4], uint32_t mask, uint32_t c, uint32_t i,
+                                            uint32_t g, uint32_t tag, const InstDev& in)
+{
+    const uint4 w = philox10(make_uint4(c, i, g, tag | (in.sid << 8)), in.k0, in.k1);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (mask & (1u << m)) v[m] = fresh_f32(word_of(w, m), in);
+}
+__device__ __forceinline__ void fresh_chunk(double (&v)[4], uint32_t mask, uint32_t c, uint32_t i,
+                                            uint32_t g, uint32_t tag, const InstDev& in)
+{
+    if (mask & 3u) {
+        const uint4 w = philox10(make_uint4(2u * c, i, g, tag | (in.sid << 8)), in.k0, in.k1);
+        if (mask & 1u) v[0] = fresh_f64(w.x, w.y, in);
+        if (mask & 2u) v[1] = fresh_f64(w.z, w.w, in);
+    }
+    if (mask & 12u) {
+        const uint4 w = philox10(make_uint4(2u * c + 1u, i, g, tag | (in.sid << 8)), in.k0, in.k1);
+        if (mask & 4u) v[2] = fresh_f64(w.x, w.y, in);
+        if (mask & 8u) v[3] = fresh_f64(w.z, w.w, in);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 fitness of one particle held by a group of G lanes (x: the lane's
+// chunks lane_g + 32 q).  Order: per-lane partials in ascending variable index
+// from +0.0, then an xor butterfly -- bit-identical to the oracle's 32-lane
+// order, since lanes beyond the group hold no variables (their partial is +0.0).
+template <class Pos, int MAXC>
+__device__ double fit64(const InstDev& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
+                        int G)
+{
+    const int D = in.D, fn = in.fn, nch = in.nchunks;
+    double acc = 0.0, acc2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        double dn = 0.0;   // Rosenbrock: d of variable 4c+4 (first of chunk c+1)
+        if (fn == FN_ROSENBROCK) {
+            const double first = (c < nch) ? __dsub_rn((double)x[q][0], __ldg(in.o64 + 4 * c)) : 0.0;
+            dn = __shfl_down_sync(gmask, first, 1, G);
+            if (G == 32 && q + 1 < MAXC) {
+                const int cn = c + 32;
+                const double nxt = (cn < nch) ? __dsub_rn((double)x[(q + 1) % MAXC][0],
+                                                          __ldg(in.o64 + 4 * cn))
+                                              : 0.0;
+                const double wrap = __shfl_sync(gmask, nxt, 0, 32);
+                if (lane_g == 31) dn = wrap;
+            }
+        }
+        if (c < nch) {
+            double dv[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * c + m;
+                dv[m] = (j < D) ? __dsub_rn((double)x[q][m], __ldg(in.o64 + j)) : 0.0;
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * c + m;
+                if (j >= D) break;
+                const double z = dv[m];
+                switch (fn) {
+                case FN_SPHERE:
+                    acc = __fma_rn(z, z, acc);
+                    break;
+                case FN_ELLIPSOID:
+                    acc = __fma_rn(__ldg(in.w64 + j), __dmul_rn(z, z), acc);
+                    break;
+                case FN_RASTRIGIN: {
+                    const double s2 = sinpi_sq_f64(z);
+                    acc = __dadd_rn(acc, __fma_rn(z, z, __dmul_rn(20.0, s2)));
+                    break;
+                }
+                case FN_ROSENBROCK:
+                    if (j < D - 1) {
+                        const double d1 = (m < 3) ? dv[(m + 1) & 3] : dn;
+                        const double a0 = __dadd_rn(z, 1.0), a1 = __dadd_rn(d1, 1.0);
+                        const double u = __fma_rn(-a0, a0, a1);
+                        acc = __dadd_rn(acc, __fma_rn(__dmul_rn(100.0, u), u, __dmul_rn(z, z)));
+                    }
+                    break;
+                case FN_ACKLEY: {
+                    acc = __fma_rn(z, z, acc);
+                    const double s = sinpi_reduced_f64(__dsub_rn(z, rint(z)));
+                    acc2 = __fma_rn(s, s, acc2);
+                    break;
+                }
+                default:
+                    break;
+                }
+            }
+        }
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(gmask, acc, off, G));
+    if (fn != FN_ACKLEY) return acc;
+    for (int off = G >> 1; off > 0; off >>= 1) acc2 = __dadd_rn(acc2, __shfl_xor_sync(gmask, acc2, off, G));
+    const double Dd = (double)D;
+    const double A = __dsqrt_rn(__ddiv_rn(acc, Dd));
+    const double B = expm1_f64(__dmul_rn(-0.2, A));
+    const double C = expm1_f64(__dmul_rn(-2.0, __ddiv_rn(acc2, Dd)));
+    return -__dadd_rn(__dmul_rn(20.0, B), __dmul_rn(0x1.5bf0a8b145769p+1, C));  // e
+}
+
+// ---------------------------------------------------------------------------
+// FP32 fitness with a rigorous bound E on |f - f_oracle| (f_oracle: the FP64
+// value of the oracle).  Terms in FP32; per-function bounds:
+//   sphere      t = z^2:        3.1u t   (z = fl(x - o), product)
+//   ellipsoid   t = w z^2:      5.2u t   (+ w rounded to float)
+//   Rastrigin   t = z^2 + 20 s^2: (2 e_sin + 3 + 16.1 + 1) u t, where 16.1u t
+//               bounds the effect of rounding z (|t'(z)| |dz| <= 2u z^2 +
+//               40 pi u |z||s| and |z||s| <= t / (2 sqrt 20))
+//   Rosenbrock  running per-term bound from |d|, |a|, |u| (see below)
+//   Ackley      bounds on S1 = sum z^2 and Q = sum s^2 propagated through the
+//               tail (|d log f1 / d log S1| <= 1/2; |d f2 / d Q| <= 2e/D)
+// plus the summation bound (K + L + 2) u sum|t| (K terms per lane, L butterfly
+// levels), a 10% margin for the rounding of E itself, and 2^-40 sum|t| for
+// the FP64 oracle's own rounding.
+struct Fit32 {
+    float f, E;
+};
+
+template <int MAXC>
+__device__ Fit32 fit32(const InstDev& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
+                       int G)
+{
+    const int D = in.D, fn = in.fn, nch = in.nchunks;
+    float acc = 0.f, acc2 = 0.f, accE = 0.f, accZ = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        float dn = 0.f;
+        if (fn == FN_ROSENBROCK) {
+            const float first = (c < nch) ? __fsub_rn(x[q][0], __ldg(in.o32 + 4 * c)) : 0.f;
+            dn = __shfl_down_sync(gmask, first, 1, G);
+            if (G == 32 && q + 1 < MAXC) {
+                const int cn = c + 32;
+                const float nxt = (cn < nch) ? __fsub_rn(x[(q + 1) % MAXC][0], __ldg(in.o32 + 4 * cn))
+                                             : 0.f;
+                const float wrap = __shfl_sync(gmask, nxt, 0, 32);
+                if (lane_g == 31) dn = wrap;
+            }
+        }
+        if (c < nch) {
+            float dv[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * c + m;
+                dv[m] = (j < D) ? __fsub_rn(x[q][m], __ldg(in.o32 + j)) : 0.f;
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * c + m;
+                if (j >= D) break;
+                const float z = dv[m];
+                switch (fn) {
+                case FN_SPHERE:
+                    acc = __fadd_rn(acc, __fmul_rn(z, z));
+                    break;
+                case FN_ELLIPSOID:
+                    acc = __fadd_rn(acc, __fmul_rn(__ldg(in.w32 + j), __fmul_rn(z, z)));
+                    break;
+                case FN_RASTRIGIN: {
+                    const float s = sinpi_reduced_f32(__fsub_rn(z, rintf(z)));
+                    acc = __fadd_rn(acc, __fmaf_rn(z, z, __fmul_rn(20.f, __fmul_rn(s, s))));
+                    break;
+                }
+                case FN_ROSENBROCK:
+                    if (j < D - 1) {
+                        // a_{j+1} - a_j^2 with a = d + 1 equals d1 - d0 (d0 + 2): evaluated
+                        // from d directly, free of the cancellation against 1.
+                        const float d1 = (m < 3) ? dv[(m + 1) & 3] : dn;
+                        const float s0 = __fadd_rn(z, 2.f);
+                        const float u = __fmaf_rn(-z, s0, d1);
+                        const float d2 = __fmul_rn(z, z);
+                        const float t = __fmaf_rn(__fmul_rn(100.f, u), u, d2);
+                        acc = __fadd_rn(acc, t);
+                        // d~ = fl(x - o): |d~ - d| <= u|d~|(1 + 2u)
+                        const float e0 = 1.01f * U32 * fabsf(z), e1 = 1.01f * U32 * fabsf(d1);
+                        // |u~ - u| <= u|u~| + e1 + |d0~| (u|s0~| + e0) + (|s0~| + e0) e0
+                        const float as0 = fabsf(s0);
+                        const float eu = 1.01f * (U32 * fabsf(u) + e1 + fabsf(z) * (U32 * as0 + e0) +
+                                                  (1.01f * as0 + e0) * e0);
+                        // 100 u^2 + d^2: propagated part plus the roundings of the tail
+                        float et = 100.f * eu * (2.f * fabsf(u) + eu) + 3.f * U32 * 100.f * u * u +
+                                   3.1f * U32 * d2 + U32 * t;
+                        // the FP64 reference forms a = d + 1 first: its own error on u is
+                        // at most 2^-51 (|a1| + 2 a0^2 + |u| + 2), a ~ |d| + 1
+                        const float a0 = fabsf(z) + 1.f, a1 = fabsf(d1) + 1.f;
+                        const float eu64 = 0x1p-51f * (a1 + 2.f * a0 * a0 + fabsf(u) + 2.f);
+                        et += 200.f * fabsf(u) * eu64 + 100.f * eu64 * eu64 + 0x1p-50f * t;
+                        accE = __fadd_rn(accE, et);
+                    }
+                    break;
+                case FN_ACKLEY: {
+                    acc = __fadd_rn(acc, __fmul_rn(z, z));
+                    const float s = sinpi_reduced_f32(__fsub_rn(z, rintf(z)));
+                    acc2 = __fadd_rn(acc2, __fmul_rn(s, s));
+                    accZ = __fadd_rn(accZ, fabsf(z));
+                    break;
+                }
+                default:
+                    break;
+                }
+            }
+        }
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(gmask, acc, off, G));
+    const float L = (float)(__ffs(G) - 1);
+    const float csum = (float)(4 * MAXC) + L + 2.f;
+    Fit32 r;
+    switch (fn) {
+    case FN_SPHERE:
+        r.f = acc;
+        r.E = 1.1f * (3.1f + csum) * U32 * acc;
+        break;
+    case FN_ELLIPSOID:
+        r.f = acc;
+        r.E = 1.1f * (5.2f + csum) * U32 * acc;
+        break;
+    case FN_RASTRIGIN:
+        r.f = acc;
+        r.E = 1.1f * (2.f * SINPI32_ERR_U + 3.f + 16.1f + 1.f + csum) * U32 * acc;
+        break;
+    case FN_ROSENBROCK:
+        for (int off = G >> 1; off > 0; off >>= 1)
+            accE = __fadd_rn(accE, __shfl_xor_sync(gmask, accE, off, G));
+        r.f = acc;
+        r.E = 1.1f * (accE + csum * U32 * acc);
+        break;
+    default: {   // Ackley
+        for (int off = G >> 1; off > 0; off >>= 1) {
+            acc2 = __fadd_rn(acc2, __shfl_xor_sync(gmask, acc2, off, G));
+            accZ = __fadd_rn(accZ, __shfl_xor_sync(gmask, accZ, off, G));
+        }
+        const float Df = (float)D;
+        const float A = __fsqrt_rn(__fdiv_rn(acc, Df));
+        const float B = expm1_f32(__fmul_rn(-0.2f, A));
+        const float C = expm1_f32(__fmul_rn(-2.f, __fdiv_rn(acc2, Df)));
+        const float f1 = __fmul_rn(-20.f, B), f2 = __fmul_rn(-0x1.5bf0a8p+1f, C);
+        r.f = __fadd_rn(f1, f2);
+        const float relS = (3.1f + csum) * U32;
+        const float EQ = 1.01f * 3.14159275f * U32 * accZ +
+                         (2.f * SINPI32_ERR_U + 1.f + csum) * U32 * acc2;
+        r.E = 1.1f * (0.5f * relS * f1 + (EXPM1F_ERR_U + 6.f) * U32 * f1 +
+                      (2.f * 2.7182818f / Df) * EQ + (EXPM1F_ERR_U + 8.f) * U32 * f2 + U32 * r.f);
+        acc = r.f;
+        break;
+    }
+    }
+    r.E = __fadd_ru(r.E, 0x1p-40f * (acc + accE));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Block-level reductions (all threads get the result).
+struct MinRec {
+    double v;
+    long long i;
+};
+__device__ __forceinline__ MinRec min_rec(MinRec a, MinRec b)
+{
+    return (b.v < a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+}
+
+struct Scratch {
+    double dv[32];
+    long long iv[32];
+    float fv[32];
+    unsigned long long uv[32];
+    int flag;
+};
+
+__device__ inline MinRec block_min_rec(MinRec r, Scratch& sh)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        MinRec o;
+        o.v = __shfl_xor_sync(0xffffffffu, r.v, off);
+        o.i = __shfl_xor_sync(0xffffffffu, r.i, off);
+        r = min_rec(r, o);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { sh.dv[w] = r.v; sh.iv[w] = r.i; }
+    __syncthreads();
+    MinRec out = { sh.dv[0], sh.iv[0] };
+    for (int k = 1; k < nw; ++k) out = min_rec(out, MinRec{ sh.dv[k], sh.iv[k] });
+    return out;
+}
+
+__device__ inline float block_min_f32(float v, Scratch& sh)
+{
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh.fv[w] = v;
+    __syncthreads();
+    float out = sh.fv[0];
+    for (int k = 1; k < nw; ++k) out = fminf(out, sh.fv[k]);
+    return out;
+}
+
+__device__ inline unsigned long long block_sum_u64(unsigned long long v, Scratch& sh)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh.uv[w] = v;
+    __syncthreads();
+    unsigned long long out = 0;
+    for (int k = 0; k < nw; ++k) out += sh.uv[k];
+    return out;
+}
+
+__device__ inline long long block_max_i64(long long v, Scratch& sh)
+{
+    for (int off = 16; off > 0; off >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh.iv[w] = v;
+    __syncthreads();
+    long long out = sh.iv[0];
+    for (int k = 1; k < nw; ++k) out = max(out, sh.iv[k]);
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 fitness of a row in memory, by one full warp (32-lane layout).
+template <class Pos, int MAXC>
+__device__ double fit64_row_warp(const InstDev& in, const Pos* row, bool l2_only)
+{
+    const int lane = threadIdx.x & 31;
+    Pos x[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane + 32 * q;
+        if (c < in.nchunks) {
+            if (l2_only) ld4_cg(row + 4 * c, x[q]); else ld4(row + 4 * c, x[q]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) x[q][m] = Pos(0);
+        }
+    }
+    return fit64<Pos, MAXC>(in, x, lane, 0xffffffffu, 32);
+}
+
+template <class Pos>
+__device__ double fit64_row(const InstDev& in, const Pos* row, bool l2_only)
+{
+    switch (in.maxc) {
+    case 1: return fit64_row_warp<Pos, 1>(in, row, l2_only);
+    case 2: return fit64_row_warp<Pos, 2>(in, row, l2_only);
+    case 4: return fit64_row_warp<Pos, 4>(in, row, l2_only);
+    default: return fit64_row_warp<Pos, 8>(in, row, l2_only);
+    }
+}
+
+__device__ __forceinline__ float f64_to_f32_rd(double v) { return __double2float_rd(v); }
+__device__ __forceinline__ float f64_to_f32_ru(double v) { return __double2float_ru(v); }
+
+}  // namespace psso
