@@ -133,7 +133,10 @@ typedef struct {
                                    run out and psso_run reports PSSO_ERR_TIMEOUT     */
     int32_t residency;          /* 0 = auto (particle state in shared memory when it
                                    fits), 2 = always stream it from global memory   */
-    int32_t reserved;           /* must be 0                                        */
+    int32_t pipeline;           /* 0 = auto: a single swarm spread over many blocks
+                                   uses a control warp that exchanges gBest while
+                                   the other warps compute the next generation;
+                                   2 = never                                        */
 } psso_config;
 
 /* One log entry (psso_get_log). */

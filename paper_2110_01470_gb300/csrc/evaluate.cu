@@ -11,7 +11,7 @@
 namespace psso {
 
 template <int MAXC>
-__device__ Fit32 fit32_row_warp(const InstDev& in, const float* row)
+__device__ Fit32 fit32_row_warp(const Hot& in, const float* row)
 {
     const int lane = threadIdx.x & 31;
     float x[MAXC][4];
@@ -29,14 +29,15 @@ __global__ void evaluate_rows(const InstDev in, const void* X, int64_t N, double
 {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= N) return;
+    const Hot h = hot_of(in);
     if constexpr (F32) {
         const float* r = static_cast<const float*>(X) + row * in.Dp;
         Fit32 v;
         switch (in.maxc) {
-        case 1: v = fit32_row_warp<1>(in, r); break;
-        case 2: v = fit32_row_warp<2>(in, r); break;
-        case 4: v = fit32_row_warp<4>(in, r); break;
-        default: v = fit32_row_warp<8>(in, r); break;
+        case 1: v = fit32_row_warp<1>(h, r); break;
+        case 2: v = fit32_row_warp<2>(h, r); break;
+        case 4: v = fit32_row_warp<4>(h, r); break;
+        default: v = fit32_row_warp<8>(h, r); break;
         }
         if ((threadIdx.x & 31) == 0) {
             f[row] = (double)v.f;
@@ -44,7 +45,7 @@ __global__ void evaluate_rows(const InstDev in, const void* X, int64_t N, double
         }
     } else {
         const double* r = static_cast<const double*>(X) + row * in.Dp;
-        const double v = fit64_row<double>(in, r, false);
+        const double v = fit64_row<double>(h, r, false);
         if ((threadIdx.x & 31) == 0) {
             f[row] = v;
             if (err) err[row] = 0.0;

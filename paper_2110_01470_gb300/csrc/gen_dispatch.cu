@@ -4,28 +4,17 @@
 
 namespace psso {
 
-cudaError_t occupancy_gen_f64_lat64(int block, size_t smem, int* n);
-cudaError_t occupancy_gen_f64_lat32(int block, size_t smem, int* n);
-cudaError_t occupancy_gen_f32r(int block, size_t smem, int* n);
-cudaError_t smem_gen_f64_lat64(size_t smem);
-cudaError_t smem_gen_f64_lat32(size_t smem);
-cudaError_t smem_gen_f32r(size_t smem);
+cudaError_t gen_f64_lat64(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
+cudaError_t gen_f64_lat32(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
+cudaError_t gen_f32r(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
 
-cudaError_t occupancy_gen(int variant, int block, size_t smem, int* blocks_per_sm)
+cudaError_t gen_call(int variant, int op, int mc_index, const KParams* p, int grid, int block,
+                     size_t smem, cudaStream_t s, int* out)
 {
     switch (variant) {
-    case 0: return occupancy_gen_f64_lat64(block, smem, blocks_per_sm);
-    case 1: return occupancy_gen_f64_lat32(block, smem, blocks_per_sm);
-    default: return occupancy_gen_f32r(block, smem, blocks_per_sm);
-    }
-}
-
-cudaError_t set_smem_gen(int variant, size_t smem)
-{
-    switch (variant) {
-    case 0: return smem_gen_f64_lat64(smem);
-    case 1: return smem_gen_f64_lat32(smem);
-    default: return smem_gen_f32r(smem);
+    case 0: return gen_f64_lat64(op, mc_index, p, grid, block, smem, s, out);
+    case 1: return gen_f64_lat32(op, mc_index, p, grid, block, smem, s, out);
+    default: return gen_f32r(op, mc_index, p, grid, block, smem, s, out);
     }
 }
 

@@ -4,16 +4,17 @@
 
 namespace psso {
 
-cudaError_t launch_gen_f32r(const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t gen_f32r(int op, int mc_index, const KParams* p, int grid, int block, size_t smem,
+                     cudaStream_t s, int* out)
 {
-    return launch_generations<float, true>(p, grid, block, smem, s);
+    return gen_entry<float, true>(op, mc_index, p, grid, block, smem, s, out);
 }
 
-cudaError_t occupancy_gen_f32r(int block, size_t smem, int* n)
+#ifdef PSSO_TRACE
+extern "C" int psso_trace_dump(void* host, size_t bytes)
 {
-    return occupancy_generations<float, true>(block, smem, n);
+    return (int)cudaMemcpyFromSymbol(host, trace_buf, bytes);
 }
-
-cudaError_t smem_gen_f32r(size_t smem) { return smem_generations<float, true>(smem); }
+#endif
 
 }  // namespace psso

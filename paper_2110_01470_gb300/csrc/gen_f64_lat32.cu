@@ -4,16 +4,10 @@
 
 namespace psso {
 
-cudaError_t launch_gen_f64_lat32(const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t gen_f64_lat32(int op, int mc_index, const KParams* p, int grid, int block, size_t smem,
+                     cudaStream_t s, int* out)
 {
-    return launch_generations<float, false>(p, grid, block, smem, s);
+    return gen_entry<float, false>(op, mc_index, p, grid, block, smem, s, out);
 }
-
-cudaError_t occupancy_gen_f64_lat32(int block, size_t smem, int* n)
-{
-    return occupancy_generations<float, false>(block, smem, n);
-}
-
-cudaError_t smem_gen_f64_lat32(size_t smem) { return smem_generations<float, false>(smem); }
 
 }  // namespace psso

@@ -4,16 +4,10 @@
 
 namespace psso {
 
-cudaError_t launch_gen_f64_lat64(const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t gen_f64_lat64(int op, int mc_index, const KParams* p, int grid, int block, size_t smem,
+                     cudaStream_t s, int* out)
 {
-    return launch_generations<double, false>(p, grid, block, smem, s);
+    return gen_entry<double, false>(op, mc_index, p, grid, block, smem, s, out);
 }
-
-cudaError_t occupancy_gen_f64_lat64(int block, size_t smem, int* n)
-{
-    return occupancy_generations<double, false>(block, smem, n);
-}
-
-cudaError_t smem_gen_f64_lat64(size_t smem) { return smem_generations<double, false>(smem); }
 
 }  // namespace psso

@@ -75,6 +75,7 @@ struct psso_ctx {
     int precision = PSSO_PREC_F64;
     int lattice = PSSO_LATTICE_F64;
     int variant = V_F64_LAT64;
+    int mc_index = 0;           // kernel width: up to 1, 2, 4, 8 chunks per lane
     size_t pos_size = 8;
     std::vector<HostInst> inst;
     std::vector<UnitDev> units;
@@ -92,13 +93,20 @@ struct psso_ctx {
 
 namespace {
 
-cudaError_t launch_variant(int v, const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t launch_variant(int v, int mc, const KParams& p, int grid, int block, size_t smem,
+                           cudaStream_t s)
 {
-    switch (v) {
-    case V_F64_LAT64: return launch_gen_f64_lat64(p, grid, block, smem, s);
-    case V_F64_LAT32: return launch_gen_f64_lat32(p, grid, block, smem, s);
-    default: return launch_gen_f32r(p, grid, block, smem, s);
-    }
+    return gen_call(v, 0, mc, &p, grid, block, smem, s, nullptr);
+}
+
+cudaError_t occupancy_of(int v, int mc, int block, size_t smem, int* n)
+{
+    return gen_call(v, 1, mc, nullptr, 0, block, smem, nullptr, n);
+}
+
+cudaError_t set_smem_of(int v, int mc, size_t smem)
+{
+    return gen_call(v, 2, mc, nullptr, 0, 0, smem, nullptr, nullptr);
 }
 
 psso_status check_problem(const psso_problem& pr, int precision, int idx)
@@ -140,8 +148,8 @@ psso_status plan(psso_ctx* h)
 {
     cudaDeviceProp prop;
     CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
-    const int TB = h->block;
-    const int nw = TB / 32;
+    int TB = h->block;
+    int nw = TB / 32;
     const int sbm = h->cfg.single_block_max == 0 ? 4 : (h->cfg.single_block_max < 0 ? 0 : h->cfg.single_block_max);
     size_t unit_smem_max = 0;
     double total_cost = 0.0;
@@ -152,10 +160,41 @@ psso_status plan(psso_ctx* h)
         I.maxc = pow2_ceil((I.nchunks + 31) / 32);
         unit_smem_max = std::max(unit_smem_max, align_up((size_t)I.Dp * h->pos_size, 16));
         total_cost += (double)I.pr.N * I.Dp;
+        h->mc_index = std::max(h->mc_index, I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0);
     }
+    int max_threads = 0;
+    CUDA_TRY(gen_call(h->variant, 3, h->mc_index, nullptr, 0, 0, 0, nullptr, &max_threads));
+    if (h->block > max_threads) {
+        if (h->cfg.threads_per_block != 0)
+            return fail(PSSO_ERR_ARG, "threads_per_block above " + std::to_string(max_threads) +
+                                          " for rows of this width");
+        h->block = max_threads;
+    }
+    // One multi-block swarm: a control warp plus enough compute warps for one
+    // particle per compute group and about one block per SM (pipelined blocks).
+    bool pipe = false;
+    if (h->inst.size() == 1 && h->cfg.pipeline != 2) {
+        const HostInst& I = h->inst[0];
+        const int gpw = 32 / I.G;
+        const int64_t groups = (I.pr.N + gpw - 1) / gpw;
+        const int64_t single_passes = (I.pr.N + (int64_t)nw * gpw - 1) / ((int64_t)nw * gpw);
+        if (single_passes > sbm) {
+            // at most 128 blocks: each lane of the control warp then polls <= 4
+            // records, all in flight at once
+            const int64_t blocks_cap = std::min<int64_t>(prop.multiProcessorCount, 128);
+            int cw = (int)std::min<int64_t>((groups + blocks_cap - 1) / blocks_cap, max_threads / 32 - 1);
+            if (h->cfg.threads_per_block != 0) cw = h->block / 32 - 1;
+            if (cw >= 1) {
+                pipe = true;
+                h->block = 32 * (cw + 1);
+            }
+        }
+    }
+    TB = h->block;
+    nw = TB / 32;
     // Occupancy with the largest single-unit footprint.
     int bps = 0;
-    CUDA_TRY(psso::occupancy_gen(h->variant, TB, unit_smem_max, &bps));
+    CUDA_TRY(occupancy_of(h->variant, h->mc_index, TB, unit_smem_max, &bps));
     if (bps < 1) return fail(PSSO_ERR_UNSUPPORTED, "kernel does not fit on one SM with this block size");
     int grid_max = bps * prop.multiProcessorCount;
     if (h->cfg.max_blocks > 0) grid_max = std::min(grid_max, h->cfg.max_blocks);
@@ -166,10 +205,22 @@ psso_status plan(psso_ctx* h)
         int64_t sumR = 0;
         for (size_t k = 0; k < h->inst.size(); ++k) {
             const HostInst& I = h->inst[k];
-            const int ppp = nw * (32 / I.G);
+            const int ppp = (pipe ? nw - 1 : nw) * (32 / I.G);
             const int64_t passes = (I.pr.N + ppp - 1) / ppp;
             int64_t r = 1;
-            if (passes > sbm) {
+            if (pipe && passes > grid_max) {     // pipelined blocks must all be co-resident
+                pipe = false;
+                h->block = h->cfg.threads_per_block ? h->cfg.threads_per_block : std::min(256, max_threads);
+                TB = h->block;
+                nw = TB / 32;
+                R.assign(h->inst.size(), 1);
+                sumR = 0;
+                k = (size_t)-1;                  // restart the loop with plain blocks
+                continue;
+            }
+            if (pipe) {
+                r = passes;
+            } else if (passes > sbm) {
                 r = (int64_t)std::floor((double)grid_max * ((double)I.pr.N * I.Dp) / total_cost);
                 r = std::max<int64_t>(1, std::min<int64_t>(r, passes));
                 r = std::min<int64_t>(r, grid_max);
@@ -183,7 +234,7 @@ psso_status plan(psso_ctx* h)
         for (size_t k = 0; k < h->inst.size(); ++k) {
             HostInst& I = h->inst[k];
             I.R = R[k];
-            const int ppp = nw * (32 / I.G);
+            const int ppp = (pipe ? nw - 1 : nw) * (32 / I.G);
             const int64_t passes = (I.pr.N + ppp - 1) / ppp;
             for (int r = 0; r < R[k]; ++r) {
                 UnitDev u{};
@@ -191,6 +242,7 @@ psso_status plan(psso_ctx* h)
                 u.rank = r;
                 u.i0 = std::min<int64_t>(I.pr.N, (passes * r / R[k]) * ppp);
                 u.i1 = std::min<int64_t>(I.pr.N, (passes * (r + 1) / R[k]) * ppp);
+                u.pipelined = (pipe && R[k] > 1) ? 1 : 0;
                 units.push_back(u);
                 cost.push_back((double)(u.i1 - u.i0) * I.Dp + 64.0 * I.Dp);
             }
@@ -249,13 +301,20 @@ psso_status plan(psso_ctx* h)
         }
         if (smem > (size_t)prop.sharedMemPerBlockOptin - 8192)
             return fail(PSSO_ERR_UNSUPPORTED, "per-block gBest rows exceed shared memory");
-        CUDA_TRY(psso::set_smem_gen(h->variant, smem));
+        CUDA_TRY(set_smem_of(h->variant, h->mc_index, smem));
         int bps2 = 0;
-        CUDA_TRY(psso::occupancy_gen(h->variant, TB, smem, &bps2));
+        CUDA_TRY(occupancy_of(h->variant, h->mc_index, TB, smem, &bps2));
         if ((int64_t)bps2 * prop.multiProcessorCount >= nblocks) {
             h->grid = nblocks;
             h->smem = smem;
             return PSSO_OK;
+        }
+        if (pipe) {           // too many blocks to be co-resident: plain blocks instead
+            pipe = false;
+            h->block = h->cfg.threads_per_block ? h->cfg.threads_per_block : std::min(256, max_threads);
+            TB = h->block;
+            nw = TB / 32;
+            continue;
         }
         grid_max = std::max(1, bps2 * prop.multiProcessorCount);
     }
@@ -325,7 +384,7 @@ psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
     p.g_end = g_end;
     p.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : (int64_t)50000000;
     p.fault_skip_rank = h->cfg.fault_skip_rank;
-    CUDA_TRY(launch_variant(h->variant, p, h->grid, h->block, h->smem, h->stream));
+    CUDA_TRY(launch_variant(h->variant, h->mc_index, p, h->grid, h->block, h->smem, h->stream));
     return PSSO_OK;
 }
 
@@ -361,14 +420,14 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     if (cfg) c = *cfg;
     if (c.precision != PSSO_PREC_F64 && c.precision != PSSO_PREC_F32_RECHECK)
         return fail(PSSO_ERR_ARG, "unknown precision");
-    if (c.threads_per_block == 0) c.threads_per_block = 256;
-    if (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32)
+    if (c.threads_per_block != 0 &&
+        (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32))
         return fail(PSSO_ERR_ARG, "threads_per_block must be a multiple of 32 in [64, 512]");
     if (c.log_stride < 0 || c.log_capacity < 0) return fail(PSSO_ERR_ARG, "negative log settings");
     if (c.log_stride > 0 && c.log_capacity == 0) return fail(PSSO_ERR_ARG, "log_capacity must be > 0");
     if (c.fault_skip_rank < 0) return fail(PSSO_ERR_ARG, "fault_skip_rank must be >= 0");
     if (c.residency != 0 && c.residency != 2) return fail(PSSO_ERR_ARG, "residency must be 0 or 2");
-    if (c.reserved != 0) return fail(PSSO_ERR_ARG, "reserved config field must be 0");
+    if (c.pipeline != 0 && c.pipeline != 2) return fail(PSSO_ERR_ARG, "pipeline must be 0 or 2");
     for (int32_t k = 0; k < count; ++k) {
         psso_status st = check_problem(problems[k], c.precision, k);
         if (st != PSSO_OK) return st;
@@ -383,7 +442,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     h->variant = c.precision == PSSO_PREC_F32_RECHECK ? V_F32R
                  : (h->lattice == PSSO_LATTICE_F32 ? V_F64_LAT32 : V_F64_LAT64);
     h->pos_size = h->lattice == PSSO_LATTICE_F32 ? 4 : 8;
-    h->block = c.threads_per_block;
+    h->block = c.threads_per_block ? c.threads_per_block : 256;
     h->stream = static_cast<cudaStream_t>(c.stream);
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
@@ -428,9 +487,9 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.off_phi = take(f32r ? N * 4 : 0);
         I.off_pver = take(N * 4);
         I.off_pflag = take(f32r ? N * 4 : 0);
-        I.off_grow = take(2 * (size_t)I.R * I.Dp * (h->pos_size / 4) * 8);   // tagged words
-        I.off_rec = take(2 * (size_t)I.R * REC_WORDS * 8);
-        I.off_rec2 = take(2 * (size_t)I.R * REC_WORDS * 8);
+        I.off_grow = take(SLOTS * (size_t)I.R * I.Dp * (h->pos_size / 4) * 8);   // tagged words
+        I.off_rec = take(SLOTS * (size_t)I.R * REC_WORDS * 8);
+        I.off_rec2 = take(SLOTS * (size_t)I.R * REC_WORDS * 8);
         I.off_gb = take(sizeof(GBestDev));
         I.off_gbrow = take(row);
         I.off_log = take(logcap * sizeof(LogDev));
@@ -464,7 +523,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     std::vector<std::vector<char>> staging;   // kept alive until the stream sync below
     for (auto& I : h->inst) {
         if (e != cudaSuccess) break;
-        const size_t rb = 2 * (size_t)I.R * REC_WORDS * 8;
+        const size_t rb = SLOTS * (size_t)I.R * REC_WORDS * 8;
         e = cudaMemsetAsync(h->arena + I.off_rec, 0xff, rb, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->arena + I.off_rec2, 0xff, rb, h->stream);
         if (e == cudaSuccess && logcap)
@@ -553,7 +612,7 @@ psso_status psso_reset(psso_handle h)
     CUDA_TRY(cudaSetDevice(h->device));
     const size_t logcap = h->cfg.log_stride > 0 ? (size_t)h->cfg.log_capacity : 0;
     for (const auto& I : h->inst) {
-        const size_t rb = 2 * (size_t)I.R * REC_WORDS * 8;
+        const size_t rb = SLOTS * (size_t)I.R * REC_WORDS * 8;
         CUDA_TRY(cudaMemsetAsync(h->arena + I.off_rec, 0xff, rb, h->stream));
         CUDA_TRY(cudaMemsetAsync(h->arena + I.off_rec2, 0xff, rb, h->stream));
         if (logcap) CUDA_TRY(cudaMemsetAsync(h->arena + I.off_log, 0xff, logcap * sizeof(LogDev), h->stream));

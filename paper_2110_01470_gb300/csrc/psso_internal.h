@@ -25,9 +25,15 @@ constexpr uint32_t TAG_INIT = 1, TAG_RHO = 2, TAG_FRESH = 3;
 // carries the low 16 bits of its generation in bits 48..63 and 48 payload
 // bits; each aligned 64-bit access is single-copy atomic, so a reader that
 // sees the expected tag in every word has read a consistent record / row
-// without any lock, atomic or writer-side fence.  Slots are double-buffered by
-// generation parity, so a 16-bit tag is unambiguous.
+// without any lock, atomic or fence.  Slots rotate over SLOTS generations: a
+// block rewrites the slot of generation g only at g + SLOTS, after it has seen
+// every block's records of g + SLOTS - 1, which those blocks published after
+// consuming generation g + SLOTS - 2's data, which they published after
+// consuming generation g's data -- two full rounds of dependent publications
+// separate a read from the overwrite of its slot.  A reader that saw a newer
+// tag would wait (and report a timeout); it can never use wrong data.
 constexpr int REC_WORDS = 6;
+constexpr int SLOTS = 3;
 enum RecWord {
     RW_IDX = 0,   // bits 0..31 particle index, bit 32 = FP64 value present
     RW_VER,       // generation the row was last written
@@ -89,9 +95,9 @@ struct InstDev {
     float* phi;
     uint32_t* pver;               // generation each pBest row was last written
     uint32_t* pflag;              // F32 mode: bit 0 = pf64 valid
-    void* grow;                   // exchange rows [2][R][Dp]
-    uint64_t* rec;                // exchange records [2][R][REC_WORDS]
-    uint64_t* rec2;               // second-round records [2][R][REC_WORDS]
+    void* grow;                   // exchange rows [SLOTS][R][Dp] (tagged words)
+    uint64_t* rec;                // exchange records [SLOTS][R][REC_WORDS]
+    uint64_t* rec2;               // second-round records [SLOTS][R][REC_WORDS]
     GBestDev* gb;
     void* gbrow;                  // gBest row [Dp]
     LogDev* log;
@@ -107,7 +113,7 @@ struct UnitDev {
     int32_t smem_off;             // byte offset of this unit's gBest row in shared memory
     int32_t resident;             // 1: X, P and pBest state live in shared memory
     int32_t res_off;              // byte offset of the resident state
-    int32_t pad;
+    int32_t pipelined;            // 1: warp 0 exchanges while warps 1.. compute ahead
 };
 
 // Shared-memory layout of a resident unit of n particles (X, P, pf64, plo,
@@ -130,14 +136,13 @@ struct KParams {
     int32_t pad;
 };
 
-// Launchers (one translation unit per kernel variant).
-cudaError_t launch_gen_f64_lat64(const KParams& p, int grid, int block, size_t smem,
-                                 cudaStream_t s);
-cudaError_t launch_gen_f64_lat32(const KParams& p, int grid, int block, size_t smem,
-                                 cudaStream_t s);
-cudaError_t launch_gen_f32r(const KParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t occupancy_gen(int variant, int block, size_t smem, int* blocks_per_sm);
-cudaError_t set_smem_gen(int variant, size_t smem);
+// Generation-kernel entry points.  variant: 0 = FP64 fitness with double
+// positions, 1 = FP64 fitness with float positions, 2 = FP32 fitness with FP64
+// recheck.  mc_index: 0..3 = up to 1, 2, 4, 8 chunks per lane.  op: 0 = launch,
+// 1 = occupancy (blocks per SM into *out), 2 = set the dynamic shared-memory
+// limit, 3 = maximum threads per block into *out.
+cudaError_t gen_call(int variant, int op, int mc_index, const KParams* p, int grid, int block,
+                     size_t smem, cudaStream_t s, int* out);
 cudaError_t launch_best_f64(const InstDev* inst, int n_inst, int lattice, cudaStream_t s);
 
 // Records the calling thread's last error message (psso_last_error).

@@ -89,9 +89,40 @@ __device__ __forceinline__ bool same_bits(double a, double b)
     return __double_as_longlong(a) == __double_as_longlong(b);
 }
 
+// The per-particle fields of an instance descriptor, as a small value type
+// that the inlined hot path keeps in registers.
+struct Hot {
+    int fn, D, Dp, nchunks, G, maxc;
+    uint32_t Tg32, Tp32, Tw32;    // thresholds, saturated at 2^32 - 1
+    uint32_t tfull;               // bit 0/1/2: Tg/Tp/Tw equal 2^32 (always taken)
+    uint32_t k0, k1, sid;
+    float S32, L32, lbf, ubf;
+    double lb, ub, span;
+    const double* o64;
+    const float* o32;
+    const double* w64;
+    const float* w32;
+};
+
+__device__ __forceinline__ Hot hot_of(const InstDev& d)
+{
+    Hot h;
+    h.fn = d.fn; h.D = d.D; h.Dp = d.Dp; h.nchunks = d.nchunks; h.G = d.G; h.maxc = d.maxc;
+    h.Tg32 = d.Tg >= 0x100000000ULL ? 0xffffffffu : (uint32_t)d.Tg;
+    h.Tp32 = d.Tp >= 0x100000000ULL ? 0xffffffffu : (uint32_t)d.Tp;
+    h.Tw32 = d.Tw >= 0x100000000ULL ? 0xffffffffu : (uint32_t)d.Tw;
+    h.tfull = (d.Tg >= 0x100000000ULL ? 1u : 0u) | (d.Tp >= 0x100000000ULL ? 2u : 0u) |
+              (d.Tw >= 0x100000000ULL ? 4u : 0u);
+    h.k0 = d.k0; h.k1 = d.k1; h.sid = d.sid;
+    h.S32 = d.S32; h.L32 = d.L32; h.lbf = d.lbf; h.ubf = d.ubf;
+    h.lb = d.lb; h.ub = d.ub; h.span = d.span;
+    h.o64 = d.o64; h.o32 = d.o32; h.w64 = d.w64; h.w32 = d.w32;
+    return h;
+}
+
 // ---------------------------------------------------------------------------
 // Fresh values (last branch of Eq. 2.1; the initial population).
-__device__ __forceinline__ float fresh_f32(uint32_t w, const InstDev& in)
+__device__ __forceinline__ float fresh_f32(uint32_t w, const Hot& in)
 {
     const float u = __fmul_rn((float)(w >> 8), 0x1p-24f);
     float x = __fmaf_rn(in.S32, u, in.L32);
@@ -99,7 +130,7 @@ __device__ __forceinline__ float fresh_f32(uint32_t w, const InstDev& in)
     x = (x > in.ubf) ? in.ubf : x;
     return x;
 }
-__device__ __forceinline__ double fresh_f64(uint32_t lo, uint32_t hi, const InstDev& in)
+__device__ __forceinline__ double fresh_f64(uint32_t lo, uint32_t hi, const Hot& in)
 {
     const uint64_t m = ((((uint64_t)hi) << 32) | lo) >> 11;
     const double u = __dmul_rn(__ull2double_rn(m), 0x1p-53);
@@ -111,7 +142,7 @@ __device__ __forceinline__ double fresh_f64(uint32_t lo, uint32_t hi, const Inst
 
 // Fresh values for the chunk's variables selected by `mask` (bit m = variable 4c+m).
 __device__ __forceinline__ void fresh_chunk(float (&v)[4], uint32_t mask, uint32_t c, uint32_t i,
-                                            uint32_t g, uint32_t tag, const InstDev& in)
+                                            uint32_t g, uint32_t tag, const Hot& in)
 {
     const uint4 w = philox10(make_uint4(c, i, g, tag | (in.sid << 8)), in.k0, in.k1);
 #pragma unroll
@@ -119,7 +150,7 @@ __device__ __forceinline__ void fresh_chunk(float (&v)[4], uint32_t mask, uint32
         if (mask & (1u << m)) v[m] = fresh_f32(word_of(w, m), in);
 }
 __device__ __forceinline__ void fresh_chunk(double (&v)[4], uint32_t mask, uint32_t c, uint32_t i,
-                                            uint32_t g, uint32_t tag, const InstDev& in)
+                                            uint32_t g, uint32_t tag, const Hot& in)
 {
     if (mask & 3u) {
         const uint4 w = philox10(make_uint4(2u * c, i, g, tag | (in.sid << 8)), in.k0, in.k1);
@@ -139,7 +170,7 @@ __device__ __forceinline__ void fresh_chunk(double (&v)[4], uint32_t mask, uint3
 // from +0.0, then an xor butterfly -- bit-identical to the oracle's 32-lane
 // order, since lanes beyond the group hold no variables (their partial is +0.0).
 template <class Pos, int MAXC>
-__device__ double fit64(const InstDev& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
+__device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
                         int G)
 {
     const int D = in.D, fn = in.fn, nch = in.nchunks;
@@ -233,7 +264,7 @@ struct Fit32 {
 };
 
 template <int MAXC>
-__device__ Fit32 fit32(const InstDev& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
+__device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
                        int G)
 {
     const int D = in.D, fn = in.fn, nch = in.nchunks;
@@ -439,7 +470,7 @@ __device__ inline long long block_max_i64(long long v, Scratch& sh)
 // ---------------------------------------------------------------------------
 // FP64 fitness of a row in memory, by one full warp (32-lane layout).
 template <class Pos, int MAXC>
-__device__ double fit64_row_warp(const InstDev& in, const Pos* row, bool l2_only)
+__device__ double fit64_row_warp(const Hot& in, const Pos* row, bool l2_only)
 {
     const int lane = threadIdx.x & 31;
     Pos x[MAXC][4];
@@ -457,7 +488,7 @@ __device__ double fit64_row_warp(const InstDev& in, const Pos* row, bool l2_only
 }
 
 template <class Pos>
-__device__ double fit64_row(const InstDev& in, const Pos* row, bool l2_only)
+__device__ double fit64_row(const Hot& in, const Pos* row, bool l2_only)
 {
     switch (in.maxc) {
     case 1: return fit64_row_warp<Pos, 1>(in, row, l2_only);

@@ -28,7 +28,26 @@
 #pragma once
 #include "sso_common.cuh"
 
+
 namespace psso {
+
+// Optional phase timestamps (global timer, ns) for profiling builds compiled
+// with -DPSSO_TRACE; the default build compiles them out.
+#ifdef PSSO_TRACE
+constexpr int TRACE_BLOCKS = 160, TRACE_GENS = 64, TRACE_POINTS = 12;
+constexpr int64_t TRACE_G0 = 100;
+__device__ unsigned long long trace_buf[TRACE_BLOCKS][TRACE_GENS][TRACE_POINTS];
+__device__ __forceinline__ void trace_point(int64_t g, int k)
+{
+    if (threadIdx.x == 0 && blockIdx.x < TRACE_BLOCKS && g >= TRACE_G0 && g < TRACE_G0 + TRACE_GENS) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        trace_buf[blockIdx.x][g - TRACE_G0][k] = t;
+    }
+}
+#else
+__device__ __forceinline__ void trace_point(int64_t, int) {}
+#endif
 
 // ---------------------------------------------------------------------------
 // Tagged words.
@@ -42,13 +61,25 @@ __device__ __forceinline__ bool tagged(uint64_t w, uint32_t tag)
 }
 __device__ __forceinline__ void ldv2(const uint64_t* p, uint64_t& a, uint64_t& b)
 {
-    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 __device__ __forceinline__ void stv2(uint64_t* p, uint64_t a, uint64_t b)
 {
-    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ int slot_of(int64_t g) { return (int)(g % SLOTS); }
+
+// Named block barriers (0 is __syncthreads): producers arrive, consumers wait.
+constexpr int BAR_VERDICT = 1;   // control warp -> compute warps: gBest of g-1 decided
+constexpr int BAR_CAND = 2;      // compute warps -> control warp: candidates of g written
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 // Words per position in a published row.
 template <class Pos> struct WordsPer;
@@ -263,192 +294,343 @@ __device__ __forceinline__ Cand cand_of(long long i, double f64, float lo, float
 struct BlockShared {
     Cand warp_cand[16];
     unsigned long long warp_acc[16], warp_rck[16];
-    Cand result;
-    unsigned long long acc, rck;
     int flag;
+    int row_changed;                      // step A replaced the gBest row in gs
     long long idx[MAX_UNITS_PER_BLOCK];   // identity (index, version) of the row in gs
     uint32_t ver[MAX_UNITS_PER_BLOCK];
 };
 
-// Block-wide candidate + counters; the result is in sh.result / sh.acc / sh.rck.
+// Warp reduction of candidates over xor offsets 16 .. first_off: only the keys
+// travel (value / bounds and index); the full winner is then read from the lane
+// that owns it.  Lanes whose xor partners at those offsets all hold
+// candidates (lane 0 in particular) end with the result.
 template <bool F32R>
-__device__ void block_cand(Cand c, unsigned long long acc, unsigned long long rck, BlockShared& sh)
+__device__ __forceinline__ Cand cand_warp_reduce(const Cand& c, int first_off, int top_off = 16)
 {
-    c = cand_warp<F32R>(c);
-    for (int off = 16; off > 0; off >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        rck += __shfl_xor_sync(0xffffffffu, rck, off);
-    }
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        sh.warp_cand[w] = c;
-        sh.warp_acc[w] = acc;
-        sh.warp_rck[w] = rck;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Cand r = sh.warp_cand[0];
-        unsigned long long a = sh.warp_acc[0], k = sh.warp_rck[0];
-        for (int q = 1; q < nw; ++q) {
-            r = cand_merge<F32R>(r, sh.warp_cand[q]);
-            a += sh.warp_acc[q];
-            k += sh.warp_rck[q];
+    double kv = c.v;
+    long long ki = c.i;
+    float kmh = c.mh, kl1 = c.l1, kl2 = c.l2;
+    for (int off = top_off; off >= first_off; off >>= 1) {
+        const long long oi = __shfl_xor_sync(0xffffffffu, ki, off);
+        if (!F32R) {
+            const double ov = __shfl_xor_sync(0xffffffffu, kv, off);
+            if (ov < kv || (ov == kv && oi < ki)) { kv = ov; ki = oi; }
+        } else {
+            const float omh = __shfl_xor_sync(0xffffffffu, kmh, off);
+            const float ol1 = __shfl_xor_sync(0xffffffffu, kl1, off);
+            const float ol2 = __shfl_xor_sync(0xffffffffu, kl2, off);
+            const bool ofirst = (ol1 < kl1) || (ol1 == kl1 && oi < ki);
+            const float l2 = ofirst ? fminf(fminf(ol2, kl1), kl2) : fminf(fminf(kl2, ol1), ol2);
+            if (ofirst) { kl1 = ol1; ki = oi; }
+            kl2 = l2;
+            kmh = fminf(kmh, omh);
         }
-        sh.result = r;
-        sh.acc = a;
-        sh.rck = k;
     }
-    __syncthreads();
+    const long long wi = __shfl_sync(0xffffffffu, ki, 0);
+    const unsigned own = __ballot_sync(0xffffffffu, c.i == wi);
+    const int src = own ? __ffs(own) - 1 : 0;
+    Cand r;
+    r.i = wi;
+    r.v = __shfl_sync(0xffffffffu, c.v, src);
+    r.l1 = __shfl_sync(0xffffffffu, c.l1, src);
+    r.h1 = __shfl_sync(0xffffffffu, c.h1, src);
+    r.ver = __shfl_sync(0xffffffffu, c.ver, src);
+    r.has1 = __shfl_sync(0xffffffffu, c.has1, src);
+    r.rank = __shfl_sync(0xffffffffu, c.rank, src);
+    r.mh = __shfl_sync(0xffffffffu, kmh, 0);
+    r.l2 = __shfl_sync(0xffffffffu, kl2, 0);
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
 // ---------------------------------------------------------------------------
-// Step B: update, evaluate and pBest-update every particle of the unit; each
-// lane returns its group's arg-min candidate.
-template <class Pos, bool F32R, int MAXC>
-__device__ Cand step_b(const InstDev& in, const UnitDev& un, const View<Pos>& v,
-                       const Pos* __restrict__ gs, int64_t g, unsigned long long& n_acc,
-                       unsigned long long& n_rck)
-{
-    const int G = in.G;
-    const int lane = threadIdx.x & 31;
-    const int lane_g = lane & (G - 1);
-    const int gpw = 32 / G;
-    const int ngroups = (blockDim.x >> 5) * gpw;
-    const int gid = (threadIdx.x >> 5) * gpw + lane / G;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const int64_t n = un.i1 - un.i0;
-    const uint32_t gg = (uint32_t)g;
-    Cand best = cand_none();
+// Step B for one particle, split into a pure part (compute: the new position,
+// its fitness, the pBest decision and the resulting state, all in registers)
+// and the stores (commit).  The split lets a block compute generation g while
+// the records of generation g-1 are still travelling, assuming the gBest row it
+// holds is still current, and commit only once the records confirm it.
+template <class Pos, int MAXC>
+struct PartState {
+    Pos x[MAXC][4];     // new position chunks of this lane
+    double f64v;        // FP64 value of the resulting pBest (when has64)
+    double cachef;      // F32: exact pBest value to cache (rejected after a recheck)
+    float lo, hi;       // F32: bounds of the resulting pBest
+    uint32_t ver;       // row version of the resulting pBest
+    uint32_t rck;       // FP64 evaluations done
+    int has64;
+    bool accept;        // P <- X
+    bool wstate;        // write the pBest state (false: identical row accepted)
+    bool cachep;        // store cachef as the kept pBest's exact value
+    bool undecided;     // F32: the bounds overlap; resolved in FP64 at commit
+};
 
-    for (int64_t k = gid; k < n; k += ngroups) {
-        const int64_t i = un.i0 + k;
-        const int64_t e = i - v.base;
-        Pos* xr = v.X + e * in.Dp;
-        Pos* pr = v.P + e * in.Dp;
-        Pos x[MAXC][4];
-        bool eqp = true;
+template <class Pos, bool F32R, int MAXC>
+__device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>& v,
+                                                 const Pos* __restrict__ gs, int64_t i, int64_t e,
+                                                 int64_t g, int lane_g, unsigned gmask,
+                                                 PartState<Pos, MAXC>& s)
+{
+    const Pos* xr = v.X + e * in.Dp;
+    const Pos* pr = v.P + e * in.Dp;
+    const uint32_t gg = (uint32_t)g;
+    const uint32_t ctr3r = TAG_RHO | (in.sid << 8), ctr3f = TAG_FRESH | (in.sid << 8);
+    bool eqp = true;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        if (c < in.nchunks) {
+            const int nvalid = min(4, in.D - 4 * c);
+            const uint32_t valid = (1u << nvalid) - 1u;
+            if (g == 0) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) s.x[q][m] = Pos(0);
+                fresh_chunk(s.x[q], valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+            } else {
+                // rho block and (FP32 lattice) fresh block are independent: both
+                // are generated together so their latencies overlap.
+                const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+                uint4 fb = make_uint4(0u, 0u, 0u, 0u);
+                if (sizeof(Pos) == 4)
+                    fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+                Pos xo[4], po[4], go[4];
+                ld4(xr + 4 * c, xo);
+                ld4(pr + 4 * c, po);
+                ld4(gs + 4 * c, go);
+                uint32_t nf = 0;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const uint32_t r = word_of(rb, m);
+                    const bool lg = (r < in.Tg32) || (in.tfull & 1u);
+                    const bool lp = (r < in.Tp32) || (in.tfull & 2u);
+                    const bool lw = (r < in.Tw32) || (in.tfull & 4u);
+                    s.x[q][m] = lg ? go[m] : lp ? po[m] : xo[m];
+                    if (!lw) nf |= 1u << m;
+                }
+                nf &= valid;
+                if (nf) {
+                    if constexpr (sizeof(Pos) == 4) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (nf & (1u << m)) s.x[q][m] = (Pos)fresh_f32(word_of(fb, m), in);
+                    } else {
+                        fresh_chunk(s.x[q], nf, (uint32_t)c, (uint32_t)i, gg, TAG_FRESH, in);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (m >= nvalid) s.x[q][m] = Pos(0);
+                    eqp = eqp && same_bits(s.x[q][m], po[m]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s.x[q][m] = Pos(0);
+        }
+    }
+    s.rck = 0;
+    s.cachep = false;
+    s.cachef = 0.0;
+    s.undecided = false;
+    if constexpr (!F32R) {
+        const double f = fit64<Pos, MAXC>(in, s.x, lane_g, gmask, in.G);
+        const double pf = (g == 0) ? f : v.pf64[e];
+        s.accept = (g == 0) || (f <= pf);
+        s.wstate = s.accept;
+        s.f64v = s.accept ? f : pf;
+        s.ver = s.accept ? gg : v.pver[e];
+        s.has64 = 1;
+        s.lo = 0.f;
+        s.hi = 0.f;
+    } else {
+        const Fit32 r = fit32<MAXC>(in, s.x, lane_g, gmask, in.G);
+        s.lo = __fsub_rd(r.f, r.E);
+        s.hi = __fadd_ru(r.f, r.E);
+        s.has64 = 0;
+        s.f64v = 0.0;
+        s.wstate = true;
+        if (g == 0) {
+            s.accept = true;
+        } else {
+            const float plo = v.plo[e], phi = v.phi[e];
+            const uint32_t pfl = v.pflag[e];
+            const double ppf = v.pf64[e];
+            if (__all_sync(gmask, eqp)) {
+                s.accept = true;            // identical row: identical fitness, keep its state
+                s.wstate = false;
+                s.lo = plo; s.hi = phi; s.has64 = (int)(pfl & 1u); s.f64v = ppf;
+            } else if (s.hi < plo) {
+                s.accept = true;
+            } else if (s.lo > phi) {
+                s.accept = false;
+                s.lo = plo; s.hi = phi; s.has64 = (int)(pfl & 1u); s.f64v = ppf;
+            } else {
+                s.undecided = true;         // resolved in FP64 at commit
+                s.accept = false;
+            }
+        }
+        s.ver = (s.accept && s.wstate) ? gg : (g == 0 ? 0u : v.pver[e]);
+    }
+}
+
+// FP32 mode, bounds overlapping: the pBest decision in FP64 in the oracle's
+// order, from the committed X row and the pBest row (or its cached value).
+struct Resolved {
+    double f64v, cachef;
+    float lo, hi;
+    uint32_t rck;
+    int accept, cachep;
+};
+
+template <class Pos, int MAXC>
+__device__ __noinline__ Resolved resolve_f64(const Hot& in, const Pos* xr, const Pos* pr, bool have_p,
+                                             double ppf, int lane_g, unsigned gmask)
+{
+    Pos a[MAXC][4], b[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        if (c < in.nchunks) {
+            ld4(xr + 4 * c, a[q]);
+            ld4(pr + 4 * c, b[q]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) { a[q][m] = Pos(0); b[q][m] = Pos(0); }
+        }
+    }
+    Resolved r;
+    r.rck = 1;
+    const double fx = fit64<Pos, MAXC>(in, a, lane_g, gmask, in.G);
+    double fp = ppf;
+    if (!have_p) {
+        fp = fit64<Pos, MAXC>(in, b, lane_g, gmask, in.G);
+        r.rck = 2;
+    }
+    r.accept = fx <= fp;
+    r.f64v = r.accept ? fx : fp;
+    r.lo = f64_to_f32_rd(r.f64v);
+    r.hi = f64_to_f32_ru(r.f64v);
+    r.cachep = !r.accept;
+    r.cachef = fp;
+    return r;
+}
+
+template <class Pos, bool F32R, int MAXC>
+__device__ __forceinline__ void particle_commit(const Hot& in, const View<Pos>& v, int64_t e,
+                                                int64_t g, int lane_g, unsigned gmask,
+                                                PartState<Pos, MAXC>& s, unsigned long long& n_acc,
+                                                unsigned long long& n_rck)
+{
+    Pos* xr = v.X + e * in.Dp;
+    Pos* pr = v.P + e * in.Dp;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        if (c < in.nchunks) st4(xr + 4 * c, s.x[q]);
+    }
+    if (F32R && s.undecided) {
+        __syncwarp(gmask);
+        const Resolved r = resolve_f64<Pos, MAXC>(in, xr, pr, (v.pflag[e] & 1u) != 0, v.pf64[e], lane_g, gmask);
+        s.accept = r.accept;
+        s.has64 = 1;
+        s.f64v = r.f64v;
+        s.lo = r.lo;
+        s.hi = r.hi;
+        s.cachep = r.cachep;
+        s.cachef = r.cachef;
+        s.rck = r.rck;
+        s.ver = s.accept ? (uint32_t)g : v.pver[e];
+    }
+    if (s.accept) {
 #pragma unroll
         for (int q = 0; q < MAXC; ++q) {
             const int c = lane_g + 32 * q;
-            if (c < in.nchunks) {
-                const int nvalid = min(4, in.D - 4 * c);
-                const uint32_t valid = (1u << nvalid) - 1u;
-                if (g == 0) {
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) x[q][m] = Pos(0);
-                    fresh_chunk(x[q], valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
-                } else {
-                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg,
-                                                         TAG_RHO | (in.sid << 8)), in.k0, in.k1);
-                    Pos xo[4], po[4], go[4];
-                    ld4(xr + 4 * c, xo);
-                    ld4(pr + 4 * c, po);
-                    ld4(gs + 4 * c, go);
-                    uint32_t nf = 0;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const uint64_t r = word_of(rb, m);
-                        x[q][m] = (r < in.Tg) ? go[m] : (r < in.Tp) ? po[m] : xo[m];
-                        if (r >= in.Tw) nf |= 1u << m;
-                    }
-                    nf &= valid;
-                    if (nf) fresh_chunk(x[q], nf, (uint32_t)c, (uint32_t)i, gg, TAG_FRESH, in);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        if (m >= nvalid) x[q][m] = Pos(0);
-                        eqp = eqp && same_bits(x[q][m], po[m]);
-                    }
-                }
-                st4(xr + 4 * c, x[q]);
-            } else {
-#pragma unroll
-                for (int m = 0; m < 4; ++m) x[q][m] = Pos(0);
-            }
+            if (c < in.nchunks) st4(pr + 4 * c, s.x[q]);
         }
-
-        bool accept;
-        Cand mine;
-        if constexpr (!F32R) {
-            const double f = fit64<Pos, MAXC>(in, x, lane_g, gmask, G);
-            const double pf = (g == 0) ? f : v.pf64[e];
-            accept = (g == 0) || (f <= pf);
-            const uint32_t ver = accept ? gg : v.pver[e];
-            if (accept && lane_g == 0) {
-                v.pf64[e] = f;
-                v.pver[e] = gg;
-            }
-            mine = cand_of<false>((long long)i, accept ? f : pf, 0.f, 0.f, 1, ver);
-        } else {
-            const Fit32 r = fit32<MAXC>(in, x, lane_g, gmask, G);
-            float lo = __fsub_rd(r.f, r.E), hi = __fadd_ru(r.f, r.E);
-            int has64 = 0;
-            double f64v = 0.0;
-            bool write_state = true;
-            if (g == 0) {
-                accept = true;
-            } else {
-                const float plo = v.plo[e], phi = v.phi[e];
-                const uint32_t pfl = v.pflag[e];
-                const double ppf = v.pf64[e];
-                if (__all_sync(gmask, eqp)) {
-                    accept = true;           // identical row: identical fitness, keep its state
-                    write_state = false;
-                    lo = plo; hi = phi; has64 = (int)(pfl & 1u); f64v = ppf;
-                } else if (hi < plo) {
-                    accept = true;
-                } else if (lo > phi) {
-                    accept = false;
-                    lo = plo; hi = phi; has64 = (int)(pfl & 1u); f64v = ppf;
-                } else {
-                    // The bound cannot decide: FP64 in the oracle's order.
-                    const double fx = fit64<float, MAXC>(in, x, lane_g, gmask, G);
-                    double fp = ppf;
-                    if (!(pfl & 1u)) {
-                        float pv[MAXC][4];
-#pragma unroll
-                        for (int q = 0; q < MAXC; ++q) {
-                            const int c = lane_g + 32 * q;
-                            if (c < in.nchunks) ld4(reinterpret_cast<const float*>(pr) + 4 * c, pv[q]);
-                            else { pv[q][0] = pv[q][1] = pv[q][2] = pv[q][3] = 0.f; }
-                        }
-                        fp = fit64<float, MAXC>(in, pv, lane_g, gmask, G);
-                        if (lane_g == 0) n_rck++;
-                    }
-                    if (lane_g == 0) n_rck++;
-                    accept = fx <= fp;
-                    has64 = 1;
-                    f64v = accept ? fx : fp;
-                    lo = f64_to_f32_rd(f64v);
-                    hi = f64_to_f32_ru(f64v);
-                    if (!accept && lane_g == 0) {   // keep the pBest's exact value
-                        v.pf64[e] = fp;
-                        v.pflag[e] = 1u;
-                        v.plo[e] = lo;
-                        v.phi[e] = hi;
-                    }
-                }
-            }
-            const uint32_t ver = (accept && write_state) ? gg : (g == 0 ? 0u : v.pver[e]);
-            if (accept && lane_g == 0 && write_state) {
-                v.pver[e] = gg;
-                v.pf64[e] = has64 ? f64v : 0.0;
-                v.pflag[e] = (uint32_t)has64;
-                v.plo[e] = lo;
-                v.phi[e] = hi;
-            }
-            mine = cand_of<true>((long long)i, f64v, lo, hi, has64, ver);
-        }
-        if (accept) {
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q) {
-                const int c = lane_g + 32 * q;
-                if (c < in.nchunks) st4(pr + 4 * c, x[q]);
-            }
-            if (lane_g == 0) n_acc++;
-        }
-        best = cand_merge<F32R>(best, mine);
     }
+    if (lane_g != 0) return;
+    n_rck += s.rck;
+    if (F32R && s.cachep) {
+        v.pf64[e] = s.cachef;
+        v.pflag[e] = 1u;
+        v.plo[e] = s.lo;
+        v.phi[e] = s.hi;
+    }
+    if (s.accept) {
+        n_acc++;
+        if (s.wstate) {
+            v.pver[e] = (uint32_t)g;
+            v.pf64[e] = s.has64 ? s.f64v : 0.0;
+            if (F32R) {
+                v.pflag[e] = (uint32_t)s.has64;
+                v.plo[e] = s.lo;
+                v.phi[e] = s.hi;
+            }
+        }
+    }
+}
+
+template <class Pos, bool F32R, int MAXC>
+__device__ __forceinline__ Cand particle_cand(int64_t i, const PartState<Pos, MAXC>& s)
+{
+    return cand_of<F32R>((long long)i, s.f64v, s.lo, s.hi, s.has64, s.ver);
+}
+
+// Lane geometry of step B: G lanes per particle, groups numbered across the block.
+struct Groups {
+    int G, lane_g, ngroups, gid;
+    unsigned gmask;
+};
+__device__ __forceinline__ Groups groups_of(int G, int first_warp = 0)
+{
+    Groups q;
+    const int lane = threadIdx.x & 31;
+    const int gpw = 32 / G;
+    q.G = G;
+    q.lane_g = lane & (G - 1);
+    q.ngroups = ((blockDim.x >> 5) - first_warp) * gpw;
+    q.gid = ((threadIdx.x >> 5) - first_warp) * gpw + lane / G;
+    q.gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    return q;
+}
+
+// Folds the group leaders' candidates into lane 0 and sums the counters per warp.
+template <bool F32R>
+__device__ __forceinline__ Cand warp_fold(Cand best, int G, unsigned long long& n_acc,
+                                          unsigned long long& n_rck)
+{
+    if (G < 32) best = cand_warp_reduce<F32R>(best, G);
+    n_acc = warp_sum_u64(n_acc);
+    n_rck = warp_sum_u64(n_rck);
     return best;
+}
+
+// Step B, non-speculative: every particle of the unit, computed and committed.
+template <class Pos, bool F32R, int MAXC>
+__device__ Cand step_b(const InstDev& desc, const UnitDev& un, const View<Pos>& v,
+                       const Pos* __restrict__ gs, int64_t g, unsigned long long& n_acc,
+                       unsigned long long& n_rck)
+{
+    // Loaded once, before any store: the fields stay in registers instead of
+    // being reloaded after every store through a generic X / P pointer.
+    const Hot in = hot_of(desc);
+    const Groups gr = groups_of(in.G);
+    const int64_t n = un.i1 - un.i0;
+    Cand best = cand_none();
+    for (int64_t k = gr.gid; k < n; k += gr.ngroups) {
+        const int64_t i = un.i0 + k;
+        const int64_t e = i - v.base;
+        PartState<Pos, MAXC> st;
+        particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
+        particle_commit<Pos, F32R, MAXC>(in, v, e, g, gr.lane_g, gr.gmask, st, n_acc, n_rck);
+        if (gr.lane_g == 0) best = cand_merge<F32R>(best, particle_cand<Pos, F32R, MAXC>(i, st));
+    }
+    trace_point(g, 6);
+    return warp_fold<F32R>(best, in.G, n_acc, n_rck);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,54 +668,80 @@ __device__ inline void write_gbest(const InstDev& in, const Winner& w, int64_t g
     }
 }
 
-// Step C: the unit's winner from the per-lane candidates.  FP32 mode falls
-// back to an exact pass (FP64 for every overlapping candidate) when the
-// bounds leave more than one candidate.
-template <class Pos, bool F32R>
-__device__ Winner step_c(const InstDev& in, const UnitDev& un, const View<Pos>& v, Cand c,
-                         unsigned long long n_acc, unsigned long long n_rck, BlockShared& sh)
+// Step C, exact fallback (FP32 mode, warp 0): several particles' bounds reach
+// the smallest upper bound m; make every such candidate exact in FP64 (oracle
+// order) and return the exact lowest-index arg-min.  Rare.
+template <class Pos>
+__device__ __noinline__ Cand step_c_exact(const InstDev& in, const UnitDev un, const View<Pos> v,
+                                          float m, unsigned long long* extra)
 {
-    block_cand<F32R>(c, n_acc, n_rck, sh);
-    Cand r = sh.result;
-    unsigned long long acc = sh.acc, rck = sh.rck;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = un.i1 - un.i0;
+    const Hot hin = hot_of(in);
+    unsigned long long rck = 0;
+    for (int64_t base = 0; base < n; base += 32) {
+        const int64_t k = base + lane;
+        const int64_t e = un.i0 + k - v.base;
+        const bool need = k < n && v.plo[e] <= m && !(v.pflag[e] & 1u);
+        unsigned bm = __ballot_sync(0xffffffffu, need);
+        while (bm) {
+            const int l = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const int64_t e2 = un.i0 + base + l - v.base;
+            const double f = fit64_row<Pos>(hin, v.P + e2 * in.Dp, false);
+            if (lane == 0) {
+                v.pf64[e2] = f;
+                v.pflag[e2] = 1u;
+                v.plo[e2] = f64_to_f32_rd(f);
+                v.phi[e2] = f64_to_f32_ru(f);
+                rck++;
+            }
+            __syncwarp();
+        }
+    }
+    // The true arg-min now has an exact value; every particle without one has
+    // a lower bound above m.
+    Cand ex = cand_none();
+    for (int64_t k = lane; k < n; k += 32) {
+        const int64_t e = un.i0 + k - v.base;
+        if (v.pflag[e] & 1u) {
+            Cand q = cand_none();
+            q.v = v.pf64[e];
+            q.i = (long long)(un.i0 + k);
+            q.ver = v.pver[e];
+            ex = cand_merge<false>(ex, q);
+        }
+    }
+    Cand r = cand_warp_reduce<false>(ex, 1);
+    r.has1 = 1;
+    r.l1 = f64_to_f32_rd(r.v);
+    r.h1 = f64_to_f32_ru(r.v);
+    *extra = __shfl_sync(0xffffffffu, rck, 0);
+    return r;
+}
+
+// Step C (warp 0): the unit's winner from the per-warp candidates.
+template <class Pos, bool F32R>
+__device__ __forceinline__ Winner step_c(const InstDev& in, const UnitDev& un, const View<Pos>& v,
+                                         BlockShared& sh)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const Cand c = lane < nw ? sh.warp_cand[lane] : cand_none();   // unused slots hold none
+    int top = 1;
+    while (2 * top < nw) top <<= 1;                 // lanes >= nw hold nothing
+    unsigned long long acc = lane < nw ? sh.warp_acc[lane] : 0ull;
+    unsigned long long rck = lane < nw ? sh.warp_rck[lane] : 0ull;
+    for (int off = top; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        rck += __shfl_xor_sync(0xffffffffu, rck, off);
+    }
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    rck = __shfl_sync(0xffffffffu, rck, 0);
+    Cand r = cand_warp_reduce<F32R>(c, 1, top);
     if (F32R && r.l2 <= r.mh) {
-        // Several particles' bounds reach the smallest upper bound: make every
-        // candidate exact, then take the exact lowest-index arg-min.
-        const float m = r.mh;
-        const int64_t n = un.i1 - un.i0;
-        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         unsigned long long extra = 0;
-        for (int64_t k = warp; k < n; k += nw) {
-            const int64_t e = un.i0 + k - v.base;
-            if (v.plo[e] <= m && !(v.pflag[e] & 1u)) {
-                const double f = fit64_row<Pos>(in, v.P + e * in.Dp, false);
-                if ((threadIdx.x & 31) == 0) {
-                    v.pf64[e] = f;
-                    v.pflag[e] = 1u;
-                    v.plo[e] = f64_to_f32_rd(f);
-                    v.phi[e] = f64_to_f32_ru(f);
-                    extra++;
-                }
-            }
-        }
-        __syncthreads();
-        Cand ex = cand_none();
-        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-            const int64_t e = un.i0 + k - v.base;
-            if (v.pflag[e] & 1u) {
-                Cand q = cand_none();
-                q.v = v.pf64[e];
-                q.i = (long long)(un.i0 + k);
-                q.ver = v.pver[e];
-                ex = cand_merge<false>(ex, q);
-            }
-        }
-        block_cand<false>(ex, 0, extra, sh);
-        r = sh.result;
-        r.has1 = 1;
-        r.l1 = f64_to_f32_rd(r.v);
-        r.h1 = f64_to_f32_ru(r.v);
-        rck += sh.rck;
+        r = step_c_exact<Pos>(in, un, v, r.mh, &extra);
+        rck += extra;
     }
     Winner w;
     w.idx = r.i;
@@ -551,7 +759,6 @@ __device__ Winner step_c(const InstDev& in, const UnitDev& un, const View<Pos>& 
         w.lo = r.l1;
         w.hi = r.h1;
     }
-    __syncthreads();
     return w;
 }
 
@@ -573,102 +780,152 @@ __device__ inline void publish_record(uint64_t* rec, uint32_t tag, const Winner&
     stv2(rec + RW_ACC, tw(tag, w.acc), tw(tag, w.rck));
 }
 
+__device__ __forceinline__ bool record_ready(const uint64_t (&w)[REC_WORDS], uint32_t tag)
+{
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < REC_WORDS; ++k) ok = ok && tagged(w[k], tag);
+    return ok;
+}
+
+__device__ __forceinline__ Winner decode_record(const uint64_t (&w)[REC_WORDS])
+{
+    Winner r;
+    r.idx = (long long)(uint32_t)w[RW_IDX];
+    r.has64 = (int)((w[RW_IDX] >> 32) & 1u);
+    r.ver = (uint32_t)w[RW_VER];
+    if (r.has64) {
+        r.f64 = __longlong_as_double((long long)(((w[RW_V1] & 0xffffffffULL) << 32) | (w[RW_V0] & 0xffffffffULL)));
+        r.lo = f64_to_f32_rd(r.f64);
+        r.hi = f64_to_f32_ru(r.f64);
+    } else {
+        r.f64 = 0.0;
+        r.lo = __uint_as_float((uint32_t)w[RW_V0]);
+        r.hi = __uint_as_float((uint32_t)w[RW_V1]);
+    }
+    r.acc = w[RW_ACC] & 0xffffffffffffULL;
+    r.rck = w[RW_RCK] & 0xffffffffffffULL;
+    return r;
+}
+
+__device__ __forceinline__ void load_record(const uint64_t* rp, uint64_t (&w)[REC_WORDS])
+{
+    ldv2(rp + RW_IDX, w[0], w[1]);
+    ldv2(rp + RW_V0, w[2], w[3]);
+    ldv2(rp + RW_ACC, w[4], w[5]);
+}
+
 // Reads one record (bounded wait); returns false on timeout / abort.
 __device__ inline bool read_record(const uint64_t* rec, uint32_t tag, Winner& w, const KParams& p,
                                    const UnitDev& un)
 {
     for (int64_t it = 0;; ++it) {
-        uint64_t a, b, c, d, e, f;
-        ldv2(rec + RW_IDX, a, b);
-        ldv2(rec + RW_V0, c, d);
-        ldv2(rec + RW_ACC, e, f);
-        if (tagged(a, tag) && tagged(b, tag) && tagged(c, tag) && tagged(d, tag) && tagged(e, tag) &&
-            tagged(f, tag)) {
-            w.idx = (long long)(uint32_t)a;
-            w.has64 = (int)((a >> 32) & 1u);
-            w.ver = (uint32_t)b;
-            if (w.has64) {
-                w.f64 = __longlong_as_double((long long)(((d & 0xffffffffULL) << 32) | (c & 0xffffffffULL)));
-                w.lo = f64_to_f32_rd(w.f64);
-                w.hi = f64_to_f32_ru(w.f64);
-            } else {
-                w.f64 = 0.0;
-                w.lo = __uint_as_float((uint32_t)c);
-                w.hi = __uint_as_float((uint32_t)d);
-            }
-            w.acc = e & 0xffffffffffffULL;
-            w.rck = f & 0xffffffffffffULL;
+        uint64_t ww[REC_WORDS];
+        load_record(rec, ww);
+        if (record_ready(ww, tag)) {
+            w = decode_record(ww);
             return true;
         }
         if (should_stop(p, it)) {
             give_up(p, un);
             return false;
         }
-        if (it > 8) __nanosleep(it < 256 ? 32 : 256);
+        if (it > 16) __nanosleep(it < 512 ? 20 : 200);
     }
 }
 
-// Step A for a unit of a multi-block instance: decide the gBest of generation
-// gp from the records and make sure shared memory holds its row.  Returns
-// false when the launch is aborting.
+// Reads the records of ranks lane, lane+32, ... (up to four per pass, all
+// loads of a pass in flight together) and folds them into one candidate per
+// lane.  Returns false on timeout / abort.
+template <bool F32R>
+__device__ inline bool gather_records(const uint64_t* recs, int R, uint32_t tag, Cand& c,
+                                      unsigned long long& acc, unsigned long long& rck,
+                                      const KParams& p, const UnitDev& un)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k0 = 0; k0 * 32 < R; k0 += 4) {
+        uint32_t pend = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (lane + 32 * (k0 + q) < R) pend |= 1u << q;
+        for (int64_t it = 0; pend; ++it) {
+            uint64_t w[4][REC_WORDS];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (pend & (1u << q)) load_record(recs + (size_t)(lane + 32 * (k0 + q)) * REC_WORDS, w[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((pend & (1u << q)) && record_ready(w[q], tag)) {
+                    const Winner r = decode_record(w[q]);
+                    Cand cq = cand_of<F32R>(r.idx, r.f64, r.lo, r.hi, r.has64, r.ver);
+                    cq.rank = lane + 32 * (k0 + q);
+                    c = cand_merge<F32R>(c, cq);
+                    acc += r.acc;
+                    rck += r.rck;
+                    pend &= ~(1u << q);
+                }
+            }
+            if (!pend) break;
+            if (should_stop(p, it)) {
+                give_up(p, un);
+                return false;
+            }
+            if (it > 16) __nanosleep(it < 512 ? 20 : 200);
+        }
+    }
+    return true;
+}
+
+// Step A (warp 0) for a unit of a multi-block instance: decide the gBest of
+// generation gp from the records and make sure shared memory holds its row.
+// Sets sh.flag when the launch is aborting.
 template <class Pos, bool F32R>
-__device__ bool step_a(const KParams& p, const InstDev& in, const UnitDev& un, const View<Pos>& v,
+__device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const UnitDev& un, const View<Pos>& v,
                        int uslot, Pos* gs, int64_t gp, bool finalize, BlockShared& sh)
 {
+    const int lane = threadIdx.x & 31;
     const int R = in.R;
     const uint32_t tag = (uint32_t)gp;
-    const uint64_t* recs = in.rec + (size_t)(gp & 1) * R * REC_WORDS;
+    const uint64_t* recs = in.rec + (size_t)slot_of(gp) * R * REC_WORDS;
     constexpr int WPE = WordsPer<Pos>::value;
-    if (threadIdx.x == 0) sh.flag = 0;
-    __syncthreads();
 
     Cand c = cand_none();
-    unsigned long long sacc = 0, srck = 0;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        Winner w;
-        if (!read_record(recs + (size_t)r * REC_WORDS, tag, w, p, un)) { sh.flag = 1; break; }
-        Cand q = cand_of<F32R>(w.idx, w.f64, w.lo, w.hi, w.has64, w.ver);
-        q.rank = r;
-        c = cand_merge<F32R>(c, q);
-        sacc += w.acc;
-        srck += w.rck;
-    }
-    __syncthreads();
-    if (sh.flag) return false;
-    block_cand<F32R>(c, sacc, srck, sh);
-    Cand win = sh.result;
-    const unsigned long long tot_acc = sh.acc;
-    unsigned long long tot_rck = sh.rck;
+    unsigned long long acc = 0, rck = 0;
+    bool ok = gather_records<F32R>(recs, R, tag, c, acc, rck, p, un);
+    if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
+    trace_point(gp + 1, 5);
+    Cand win = cand_warp_reduce<F32R>(c, 1);
+    acc = warp_sum_u64(acc);
+    rck = warp_sum_u64(rck);
+    trace_point(gp + 1, 8);
 
     if (F32R && win.l2 <= win.mh) {
         // Several ranks overlap: ranks without an exact value publish it
         // (second round), then the exact lowest-index arg-min is taken.
         const float m = win.mh;
-        uint64_t* recs2 = in.rec2 + (size_t)(gp & 1) * R * REC_WORDS;
-        if (threadIdx.x < 32) {
-            Winner me;
-            const bool ok = read_record(recs + (size_t)un.rank * REC_WORDS, tag, me, p, un);
-            if (ok && me.lo <= m && !me.has64) {
-                const double f = fit64_row<Pos>(in, v.P + (me.idx - v.base) * in.Dp, false);
-                if (threadIdx.x == 0) {
-                    Winner ww = me;
-                    ww.f64 = f;
-                    ww.has64 = 1;
-                    ww.acc = 0;
-                    ww.rck = 1;
-                    publish_record(recs2 + (size_t)un.rank * REC_WORDS, tag, ww);
-                }
+        uint64_t* recs2 = in.rec2 + (size_t)slot_of(gp) * R * REC_WORDS;
+        Winner me;
+        ok = read_record(recs + (size_t)un.rank * REC_WORDS, tag, me, p, un);
+        if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
+        if (me.lo <= m && !me.has64) {
+            const double f = fit64_row<Pos>(hot_of(in), v.P + (me.idx - v.base) * in.Dp, false);
+            if (lane == 0) {
+                Winner ww = me;
+                ww.f64 = f;
+                ww.has64 = 1;
+                ww.acc = 0;
+                ww.rck = 1;
+                publish_record(recs2 + (size_t)un.rank * REC_WORDS, tag, ww);
             }
         }
-        __syncthreads();
         Cand ex = cand_none();
         unsigned long long r2 = 0;
-        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        for (int r = lane; r < R; r += 32) {
             Winner w;
-            if (!read_record(recs + (size_t)r * REC_WORDS, tag, w, p, un)) { sh.flag = 1; break; }
+            if (!read_record(recs + (size_t)r * REC_WORDS, tag, w, p, un)) { ok = false; break; }
             if (w.lo > m) continue;
             if (!w.has64) {
-                if (!read_record(recs2 + (size_t)r * REC_WORDS, tag, w, p, un)) { sh.flag = 1; break; }
+                if (!read_record(recs2 + (size_t)r * REC_WORDS, tag, w, p, un)) { ok = false; break; }
                 r2 += 1;
             }
             Cand q = cand_none();
@@ -678,55 +935,47 @@ __device__ bool step_a(const KParams& p, const InstDev& in, const UnitDev& un, c
             q.rank = r;
             ex = cand_merge<false>(ex, q);
         }
-        __syncthreads();
-        if (sh.flag) return false;
-        block_cand<false>(ex, 0, r2, sh);
-        win = sh.result;
+        if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
+        win = cand_warp_reduce<false>(ex, 1);
         win.has1 = 1;
         win.l1 = f64_to_f32_rd(win.v);
         win.h1 = f64_to_f32_ru(win.v);
-        tot_rck += sh.rck;
+        rck += warp_sum_u64(r2);
     }
 
     // Fetch the winner's row if it is not the one already in shared memory.
     const bool changed = (sh.idx[uslot] != win.i) || (sh.ver[uslot] != win.ver);
     if (changed) {
         const uint64_t* src = static_cast<const uint64_t*>(in.grow) +
-                              ((size_t)(gp & 1) * R + win.rank) * (size_t)in.Dp * WPE;
-        for (int ch = threadIdx.x; ch < in.nchunks; ch += blockDim.x) {
+                              ((size_t)slot_of(gp) * R + win.rank) * (size_t)in.Dp * WPE;
+        for (int ch = lane; ch < in.nchunks; ch += 32) {
             Pos vals[4];
             for (int64_t it = 0;; ++it) {
                 if (get_chunk(src + (size_t)4 * ch * WPE, tag, vals)) break;
-                if (should_stop(p, it)) { give_up(p, un); sh.flag = 1; break; }
-                if (it > 8) __nanosleep(64);
+                if (should_stop(p, it)) { give_up(p, un); ok = false; break; }
+                if (it > 16) __nanosleep(32);
             }
             st4(gs + 4 * ch, vals);
         }
     }
-    // Everything this block read of generation gp is complete before any of
-    // its later publications (the writers reuse these slots at gp + 2).
-    fence_acq_rel_gpu();
-    __syncthreads();
-    if (sh.flag) return false;
-    if (threadIdx.x == 0) {
-        sh.idx[uslot] = win.i;
-        sh.ver[uslot] = win.ver;
-    }
+    trace_point(gp + 1, 9);
+    if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
+    __syncwarp();
     if (un.rank == 0 && finalize) {
         if (changed) {
             Pos* dst = static_cast<Pos*>(in.gbrow);
-            for (int ch = threadIdx.x; ch < in.nchunks; ch += blockDim.x) {
+            for (int ch = lane; ch < in.nchunks; ch += 32) {
                 Pos t[4];
                 ld4(gs + 4 * ch, t);
                 st4(dst + 4 * ch, t);
             }
         }
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             Winner w;
             w.idx = win.i;
             w.ver = win.ver;
-            w.acc = tot_acc;
-            w.rck = tot_rck;
+            w.acc = acc;
+            w.rck = rck;
             w.has64 = F32R ? win.has1 : 1;
             w.f64 = F32R ? (win.has1 ? win.v : 0.0) : win.v;
             w.lo = F32R ? win.l1 : f64_to_f32_rd(win.v);
@@ -734,48 +983,52 @@ __device__ bool step_a(const KParams& p, const InstDev& in, const UnitDev& un, c
             write_gbest(in, w, gp);
         }
     }
-    __syncthreads();
-    return true;
+    if (lane == 0) {
+        sh.idx[uslot] = win.i;
+        sh.ver[uslot] = win.ver;
+        sh.row_changed = changed ? 1 : 0;
+    }
 }
 
-// Step D for a multi-block instance: publish the unit's winner row and record.
+// Step D (warp 0) for a multi-block instance: publish the unit's winner row and record.
 template <class Pos>
-__device__ void step_d_publish(const KParams& p, const InstDev& in, const UnitDev& un,
+__device__ __forceinline__ void step_d_publish(const KParams& p, const InstDev& in, const UnitDev& un,
                                const View<Pos>& v, const Winner& w, int64_t g)
 {
     if (p.fault_skip_rank > 0 && un.inst == 0 && un.rank == p.fault_skip_rank - 1) return;
     constexpr int WPE = WordsPer<Pos>::value;
+    const int lane = threadIdx.x & 31;
     const int R = in.R;
     const uint32_t tag = (uint32_t)g;
-    uint64_t* dst = static_cast<uint64_t*>(in.grow) + ((size_t)(g & 1) * R + un.rank) * (size_t)in.Dp * WPE;
+    uint64_t* dst = static_cast<uint64_t*>(in.grow) + ((size_t)slot_of(g) * R + un.rank) * (size_t)in.Dp * WPE;
     const Pos* src = v.P + (w.idx - v.base) * in.Dp;
-    for (int ch = threadIdx.x; ch < in.nchunks; ch += blockDim.x) {
+    for (int ch = lane; ch < in.nchunks; ch += 32) {
         Pos t[4];
         ld4(src + 4 * ch, t);
         put_chunk(dst + (size_t)4 * ch * WPE, tag, t);
     }
-    if (threadIdx.x == 0)
-        publish_record(in.rec + ((size_t)(g & 1) * R + un.rank) * REC_WORDS, tag, w);
+    if (lane == 0) publish_record(in.rec + ((size_t)slot_of(g) * R + un.rank) * REC_WORDS, tag, w);
 }
 
-// Step D for a whole-swarm unit: refresh the shared-memory gBest row.
+// Step D (warp 0) for a whole-swarm unit: refresh the shared-memory gBest row.
 template <class Pos>
-__device__ void step_d_local(const InstDev& in, const View<Pos>& v, const Winner& w, Pos* gs,
+__device__ __noinline__ void step_d_local(const InstDev& in, const View<Pos>& v, const Winner& w, Pos* gs,
                              int uslot, int64_t g, BlockShared& sh)
 {
+    const int lane = threadIdx.x & 31;
     const bool changed = (sh.idx[uslot] != w.idx) || (sh.ver[uslot] != w.ver);
     if (changed) {
         const Pos* src = v.P + (w.idx - v.base) * in.Dp;
         Pos* dst = static_cast<Pos*>(in.gbrow);
-        for (int ch = threadIdx.x; ch < in.nchunks; ch += blockDim.x) {
+        for (int ch = lane; ch < in.nchunks; ch += 32) {
             Pos t[4];
             ld4(src + 4 * ch, t);
             st4(gs + 4 * ch, t);
             st4(dst + 4 * ch, t);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    if (lane == 0) {
         sh.idx[uslot] = w.idx;
         sh.ver[uslot] = w.ver;
         write_gbest(in, w, g);
@@ -783,27 +1036,161 @@ __device__ void step_d_local(const InstDev& in, const View<Pos>& v, const Winner
 }
 
 // ---------------------------------------------------------------------------
-template <class Pos, bool F32R>
+template <class Pos, bool F32R, int MC>
 __device__ Cand unit_b(const InstDev& in, const UnitDev& un, const View<Pos>& v, const Pos* gs,
                        int64_t g, unsigned long long& n_acc, unsigned long long& n_rck)
 {
-    switch (in.maxc) {
-    case 1: return step_b<Pos, F32R, 1>(in, un, v, gs, g, n_acc, n_rck);
-    case 2: return step_b<Pos, F32R, 2>(in, un, v, gs, g, n_acc, n_rck);
-    case 4: return step_b<Pos, F32R, 4>(in, un, v, gs, g, n_acc, n_rck);
-    default: return step_b<Pos, F32R, 8>(in, un, v, gs, g, n_acc, n_rck);
+    if (MC == 1 || in.maxc == 1) return step_b<Pos, F32R, 1>(in, un, v, gs, g, n_acc, n_rck);
+    if (MC == 2 || in.maxc == 2) return step_b<Pos, F32R, (MC < 2 ? MC : 2)>(in, un, v, gs, g, n_acc, n_rck);
+    if (MC == 4 || in.maxc == 4) return step_b<Pos, F32R, (MC < 4 ? MC : 4)>(in, un, v, gs, g, n_acc, n_rck);
+    return step_b<Pos, F32R, MC>(in, un, v, gs, g, n_acc, n_rck);
+}
+
+// Step B overlapped with step A: each group (at most one particle per group)
+// computes generation g with the gBest row it holds, while warp 0 reads the
+// records of g-1.  If the winner's row is the one used, the results are
+// committed as computed; otherwise (the gBest moved) they are recomputed.
+template <class Pos, bool F32R, int MAXC>
+__device__ Cand spec_b(const KParams& p, const InstDev& desc, const UnitDev& un, const View<Pos>& v,
+                       Pos* gs, int slot, int64_t g, BlockShared& sh, unsigned long long& n_acc,
+                       unsigned long long& n_rck)
+{
+    const Hot in = hot_of(desc);
+    const Groups gr = groups_of(in.G);
+    const int64_t n = un.i1 - un.i0;
+    const bool have = gr.gid < n;
+    const int64_t i = un.i0 + gr.gid, e = i - v.base;
+    PartState<Pos, MAXC> st;
+    bool need = have;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        if (need) particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
+        if (pass == 1) break;
+        trace_point(g, 7);
+        if ((threadIdx.x >> 5) == 0)
+            step_a<Pos, F32R>(p, desc, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh);
+        __syncthreads();
+        if (sh.flag) return cand_none();
+        trace_point(g, 1);
+        need = have && sh.row_changed;     // the gBest moved: recompute with the new row
+        if (!need) break;
+    }
+    Cand best = cand_none();
+    if (have) {
+        particle_commit<Pos, F32R, MAXC>(in, v, e, g, gr.lane_g, gr.gmask, st, n_acc, n_rck);
+        if (gr.lane_g == 0) best = particle_cand<Pos, F32R, MAXC>(i, st);
+    }
+    trace_point(g, 6);
+    return warp_fold<F32R>(best, in.G, n_acc, n_rck);
+}
+
+template <class Pos, bool F32R, int MC>
+__device__ Cand unit_spec(const KParams& p, const InstDev& in, const UnitDev& un, const View<Pos>& v,
+                          Pos* gs, int slot, int64_t g, BlockShared& sh, unsigned long long& n_acc,
+                          unsigned long long& n_rck)
+{
+    if (MC == 1 || in.maxc == 1) return spec_b<Pos, F32R, 1>(p, in, un, v, gs, slot, g, sh, n_acc, n_rck);
+    if (MC == 2 || in.maxc == 2)
+        return spec_b<Pos, F32R, (MC < 2 ? MC : 2)>(p, in, un, v, gs, slot, g, sh, n_acc, n_rck);
+    if (MC == 4 || in.maxc == 4)
+        return spec_b<Pos, F32R, (MC < 4 ? MC : 4)>(p, in, un, v, gs, slot, g, sh, n_acc, n_rck);
+    return spec_b<Pos, F32R, MC>(p, in, un, v, gs, slot, g, sh, n_acc, n_rck);
+}
+
+// Warp-specialised pipeline for a block that owns one unit of a multi-block
+// instance with at most one particle per compute group.  Warp 0 (control)
+// runs steps C and D of generation g and step A of g (reading every block's
+// record); meanwhile warps 1.. (compute) already evaluate generation g+1 with
+// the gBest row they hold.  When the verdict of step A says the row was
+// current, their results are committed as computed; otherwise they are
+// recomputed.  Two named barriers carry the hand-offs.
+template <class Pos, bool F32R, int MAXC>
+__device__ void pipelined_unit(const KParams& p, const InstDev& desc, const UnitDev& un,
+                               const View<Pos>& v, Pos* gs, int slot, BlockShared& sh)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nth = blockDim.x;
+    if (warp == 0) {
+        for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
+            trace_point(g, 0);
+            if (g > 0) {
+                step_a<Pos, F32R>(p, desc, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh);
+            } else if (lane == 0) {
+                sh.row_changed = 0;
+            }
+            __syncwarp();
+            trace_point(g, 1);
+            bar_arrive(BAR_VERDICT, nth);
+            if (sh.flag) return;
+            bar_sync(BAR_CAND, nth);
+            trace_point(g, 2);
+            if (lane == 0) { sh.warp_cand[0] = cand_none(); sh.warp_acc[0] = 0; sh.warp_rck[0] = 0; }
+            __syncwarp();
+            const Winner w = step_c<Pos, F32R>(desc, un, v, sh);
+            trace_point(g, 3);
+            step_d_publish<Pos>(p, desc, un, v, w, g);
+            trace_point(g, 4);
+        }
+        return;
+    }
+    const Hot in = hot_of(desc);
+    const Groups gr = groups_of(in.G, 1);
+    const int64_t n = un.i1 - un.i0;
+    const bool have = gr.gid < n;
+    const int64_t i = un.i0 + gr.gid, e = i - v.base;
+    for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
+        PartState<Pos, MAXC> st;
+        if (have) particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
+        if (threadIdx.x == 32) trace_point(g, 7);
+        bar_sync(BAR_VERDICT, nth);
+        if (sh.flag) return;
+        if (have && sh.row_changed)       // the gBest moved: recompute with the new row
+            particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
+        unsigned long long n_acc = 0, n_rck = 0;
+        Cand best = cand_none();
+        if (have) {
+            particle_commit<Pos, F32R, MAXC>(in, v, e, g, gr.lane_g, gr.gmask, st, n_acc, n_rck);
+            if (gr.lane_g == 0) best = particle_cand<Pos, F32R, MAXC>(i, st);
+        }
+        best = warp_fold<F32R>(best, in.G, n_acc, n_rck);
+        if (lane == 0) {
+            sh.warp_cand[warp] = best;
+            sh.warp_acc[warp] = n_acc;
+            sh.warp_rck[warp] = n_rck;
+        }
+        if (threadIdx.x == 32) trace_point(g, 6);
+        bar_arrive(BAR_CAND, nth);
     }
 }
 
-template <class Pos, bool F32R>
-__global__ void __launch_bounds__(512) sso_generations(const KParams p)
+template <class Pos, bool F32R, int MC>
+__device__ void pipelined(const KParams& p, const InstDev& in, const UnitDev& un, const View<Pos>& v,
+                          Pos* gs, int slot, BlockShared& sh)
+{
+    if (MC == 1 || in.maxc == 1) return pipelined_unit<Pos, F32R, 1>(p, in, un, v, gs, slot, sh);
+    if (MC == 2 || in.maxc == 2) return pipelined_unit<Pos, F32R, (MC < 2 ? MC : 2)>(p, in, un, v, gs, slot, sh);
+    if (MC == 4 || in.maxc == 4) return pipelined_unit<Pos, F32R, (MC < 4 ? MC : 4)>(p, in, un, v, gs, slot, sh);
+    return pipelined_unit<Pos, F32R, MC>(p, in, un, v, gs, slot, sh);
+}
+
+// Launch bound: kernels for wide rows (4 or 8 chunks of 4 variables per lane)
+// are limited to 256 threads so that each thread may use up to 255 registers.
+template <int MC> struct GenBound { static constexpr int threads = MC >= 4 ? 256 : 512; };
+
+// Per generation and unit, warp 0 runs steps A, C and D; all warps run step B.
+// Two block barriers per generation: after step A (the gBest row is in shared
+// memory) and after step B (every particle's candidate is in shared memory).
+template <class Pos, bool F32R, int MC>
+__global__ void __launch_bounds__(GenBound<MC>::threads) sso_generations(const KParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockShared sh;
     const int u0 = p.block_first[blockIdx.x], u1 = p.block_first[blockIdx.x + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // Prologue: resident units move into shared memory; whole-swarm units
     // restore their gBest row.
+    if (threadIdx.x == 0) sh.flag = 0;
     for (int u = u0; u < u1; ++u) {
         const UnitDev un = p.units[u];
         const InstDev& in = p.inst[un.inst];
@@ -825,6 +1212,13 @@ __global__ void __launch_bounds__(512) sso_generations(const KParams p)
     }
     __syncthreads();
 
+    if (u1 - u0 == 1 && p.units[u0].pipelined) {
+        const UnitDev un = p.units[u0];
+        const InstDev& in = p.inst[un.inst];
+        Pos* gs = reinterpret_cast<Pos*>(smem + un.smem_off);
+        const View<Pos> v = make_view<Pos>(in, un, smem);
+        pipelined<Pos, F32R, MC>(p, in, un, v, gs, 0, sh);
+    } else {
     for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
         for (int u = u0; u < u1; ++u) {
             const UnitDev un = p.units[u];
@@ -832,32 +1226,54 @@ __global__ void __launch_bounds__(512) sso_generations(const KParams p)
             Pos* gs = reinterpret_cast<Pos*>(smem + un.smem_off);
             const View<Pos> v = make_view<Pos>(in, un, smem);
             const int slot = u - u0;
-            if (in.R > 1 && g > 0) {
-                if (!step_a<Pos, F32R>(p, in, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh)) return;
-            }
+            trace_point(g, 0);
+            const bool exchange = in.R > 1 && g > 0;
+            const int ngroups = (blockDim.x >> 5) * (32 / in.G);
             unsigned long long n_acc = 0, n_rck = 0;
-            const Cand c = unit_b<Pos, F32R>(in, un, v, gs, g, n_acc, n_rck);
+            Cand c;
+            if (exchange && un.i1 - un.i0 <= ngroups) {
+                c = unit_spec<Pos, F32R, MC>(p, in, un, v, gs, slot, g, sh, n_acc, n_rck);
+                if (sh.flag) return;
+            } else {
+                if (warp == 0 && exchange)
+                    step_a<Pos, F32R>(p, in, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh);
+                __syncthreads();
+                if (sh.flag) return;
+                trace_point(g, 1);
+                c = unit_b<Pos, F32R, MC>(in, un, v, gs, g, n_acc, n_rck);
+            }
+            if (lane == 0) {
+                sh.warp_cand[warp] = c;
+                sh.warp_acc[warp] = n_acc;
+                sh.warp_rck[warp] = n_rck;
+            }
             __syncthreads();
-            const Winner w = step_c<Pos, F32R>(in, un, v, c, n_acc, n_rck, sh);
-            if (in.R == 1) step_d_local<Pos>(in, v, w, gs, slot, g, sh);
-            else step_d_publish<Pos>(p, in, un, v, w, g);
-            __syncthreads();
+            trace_point(g, 2);
+            if (warp == 0) {
+                const Winner w = step_c<Pos, F32R>(in, un, v, sh);
+                trace_point(g, 3);
+                if (in.R == 1) step_d_local<Pos>(in, v, w, gs, slot, g, sh);
+                else step_d_publish<Pos>(p, in, un, v, w, g);
+            }
+            trace_point(g, 4);
         }
     }
+    }
+    __syncthreads();
     // Epilogue: finalise the last generation of multi-block instances and
     // write resident units back.
     for (int u = u0; u < u1; ++u) {
         const UnitDev un = p.units[u];
         const InstDev& in = p.inst[un.inst];
         const View<Pos> v = make_view<Pos>(in, un, smem);
-        if (in.R > 1) {
+        if (in.R > 1 && warp == 0) {
             Pos* gs = reinterpret_cast<Pos*>(smem + un.smem_off);
-            if (!step_a<Pos, F32R>(p, in, un, v, u - u0, gs, p.g_end, true, sh)) return;
+            step_a<Pos, F32R>(p, in, un, v, u - u0, gs, p.g_end, true, sh);
         }
-        if (un.resident) {
-            move_resident<Pos, F32R>(in, un, smem, false);
-            __syncthreads();
-        }
+        __syncthreads();
+        if (sh.flag) return;
+        if (un.resident) move_resident<Pos, F32R>(in, un, smem, false);
+        __syncthreads();
     }
 }
 
@@ -869,14 +1285,14 @@ __global__ void best_f64_kernel(const InstDev* inst, int n_inst)
     if (k >= n_inst) return;
     const InstDev& in = inst[k];
     if (in.gb->has64) return;
-    const double f = fit64_row<Pos>(in, static_cast<const Pos*>(in.gbrow), true);
+    const double f = fit64_row<Pos>(hot_of(in), static_cast<const Pos*>(in.gbrow), true);
     if (threadIdx.x == 0) {
         in.gb->f64 = f;
         in.gb->has64 = 1;
     }
 }
 
-template <class Pos, bool F32R>
+template <class Pos, bool F32R, int MC>
 inline cudaError_t launch_generations(const KParams& p, int grid, int block, size_t smem, cudaStream_t s)
 {
     cudaLaunchConfig_t lc = {};
@@ -889,20 +1305,44 @@ inline cudaError_t launch_generations(const KParams& p, int grid, int block, siz
     at[0].val.cooperative = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, sso_generations<Pos, F32R>, p);
+    return cudaLaunchKernelEx(&lc, sso_generations<Pos, F32R, MC>, p);
 }
 
-template <class Pos, bool F32R>
+template <class Pos, bool F32R, int MC>
 inline cudaError_t occupancy_generations(int block, size_t smem, int* n)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sso_generations<Pos, F32R>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sso_generations<Pos, F32R, MC>, block, smem);
 }
 
-template <class Pos, bool F32R>
+template <class Pos, bool F32R, int MC>
 inline cudaError_t smem_generations(size_t smem)
 {
-    return cudaFuncSetAttribute(sso_generations<Pos, F32R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)std::max<size_t>(smem, 1));
+    return cudaFuncSetAttribute(sso_generations<Pos, F32R, MC>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+}
+
+// One kernel variant: launch / occupancy / shared-memory entry points for the
+// four chunk widths (index 0..3 = 1, 2, 4, 8 chunks per lane).
+template <class Pos, bool F32R>
+inline cudaError_t gen_entry(int op, int mc_index, const KParams* p, int grid, int block, size_t smem,
+                             cudaStream_t s, int* out)
+{
+    switch (mc_index) {
+#define PSSO_GEN_CASE(IDX, MCV)                                                              \
+    case IDX:                                                                                \
+        if (op == 0) return launch_generations<Pos, F32R, MCV>(*p, grid, block, smem, s);    \
+        if (op == 1) return occupancy_generations<Pos, F32R, MCV>(block, smem, out);         \
+        if (op == 2) return smem_generations<Pos, F32R, MCV>(smem);                          \
+        *out = GenBound<MCV>::threads;                                                       \
+        return cudaSuccess;
+        PSSO_GEN_CASE(0, 1)
+        PSSO_GEN_CASE(1, 2)
+        PSSO_GEN_CASE(2, 4)
+        PSSO_GEN_CASE(3, 8)
+#undef PSSO_GEN_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace psso

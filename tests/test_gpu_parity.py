@@ -73,7 +73,8 @@ def test_fp64_bitexact(lib, fn, lattice, N, D, t):
 @pytest.mark.parametrize("cfg", [dict(), dict(single_block_max=-1), dict(max_blocks=3),
                                  dict(threads_per_block=64, single_block_max=-1),
                                  dict(threads_per_block=512), dict(residency=2),
-                                 dict(residency=2, max_blocks=5, threads_per_block=128)])
+                                 dict(residency=2, max_blocks=5, threads_per_block=128),
+                                 dict(pipeline=2), dict(threads_per_block=96)])
 def test_fp64_multiblock_bitexact(lib, cfg):
     """Swarms spread over many blocks (record exchange between blocks), several
     units per block, and other block sizes give the same trajectory."""
@@ -147,7 +148,8 @@ def test_fp32_recheck_same_decisions(lib, fn, N, D, t):
     _assert_same_decisions(g, _oracle_run(p, t), t, fn)
 
 
-@pytest.mark.parametrize("cfg", [dict(), dict(residency=2), dict(max_blocks=7)])
+@pytest.mark.parametrize("cfg", [dict(), dict(residency=2), dict(max_blocks=7), dict(pipeline=2),
+                                 dict(threads_per_block=128)])
 def test_fp32_recheck_multiblock(lib, cfg):
     p = workload.config("rastrigin_d100")["problems"][0]
     t = 60
