@@ -238,6 +238,32 @@ psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const double* X, con
                           const double* weights, const double* rotation, int32_t precision,
                           double* f, double* err, void* stream);
 
+/* Batched fitness for callers that cannot allocate device memory: code that
+ * runs while another allocator owns the device memory, code that must not let
+ * cudaMalloc / cudaFree synchronise the device in its steady state (a
+ * real-time or latency-critical loop), or code that has a fixed device-memory
+ * budget set aside up front.  The paper has no counterpart; this is a
+ * convenience of this library.
+ *
+ * Computes what psso_evaluate computes (same routines, same summation order,
+ * bit-identical results) but takes DEVICE pointers: X (N*D doubles,
+ * row-major), shift and weights (D doubles each, or NULL as in psso_problem),
+ * and the outputs f (N doubles) and err (N doubles, or NULL).  It allocates
+ * nothing: its only scratch, the padded shift / weight vectors, lives in one
+ * static device array of 24 KiB (D at most 1024; larger D is rejected with
+ * PSSO_ERR_ARG).  With PSSO_PREC_F32_RECHECK every X value must be a float;
+ * rows holding other values get NaN in f and err.
+ *
+ * Work is enqueued on `stream` (cudaStream_t, NULL = default) and the call
+ * returns without waiting.  The first call on a device looks up the scratch
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Every call shares the array and
+ * rewrites what it reads, so calls that overlap on the GPU (unordered streams)
+ * race on it. */
+psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, const double* X,
+                                  const double* shift, const double* weights, int32_t precision,
+                                  double* f, double* err, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);
 

@@ -117,6 +117,9 @@ def load(path: str = LIB_PATH):
         "psso_evaluate": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_evaluate_noalloc": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -271,6 +274,18 @@ def psso_evaluate(fn, X, shift=None, weights=None, rotation=None, precision=PSSO
     _check(load().psso_evaluate(int(fn), N, D, _ptr(X), _ptr(o), _ptr(w), _ptr(M),
                                 int(precision), _ptr(f), _ptr(e), stream))
     return f, e
+
+
+def psso_evaluate_noalloc(fn, N, D, X_ptr, shift_ptr, weights_ptr, precision, f_ptr, err_ptr,
+                          stream=None):
+    """Allocation-free batched fitness on device buffers (raw device pointers,
+    e.g. ``tensor.data_ptr()``).  Enqueued on ``stream``; does not wait."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    if isinstance(precision, str):
+        precision = PRECISION[precision]
+    _check(load().psso_evaluate_noalloc(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
+                                        int(precision), f_ptr, err_ptr, stream))
 
 
 def psso_last_error():
