@@ -61,16 +61,16 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
                                      double* err, void* stream)
 {
     using namespace psso;
-    (void)rotation;
     auto bad = [](psso_status st, const char* msg) {
         set_last_error(msg);
         return st;
     };
     if (!X || !f || N < 1 || D < 1 || D > 1024 || fn < PSSO_SPHERE || fn > PSSO_ROT_ACKLEY)
         return bad(PSSO_ERR_ARG, "psso_evaluate: need X, f, N >= 1, 1 <= D <= 1024, a known function");
-    if (fn >= PSSO_ROT_ELLIPSOID)
-        return bad(PSSO_ERR_UNSUPPORTED, "psso_evaluate: rotated functions are not available in this build");
-    if ((fn == PSSO_ELLIPSOID) && !weights) return bad(PSSO_ERR_ARG, "psso_evaluate: ellipsoid needs weights");
+    if (fn >= PSSO_ROT_ELLIPSOID && !rotation)
+        return bad(PSSO_ERR_ARG, "psso_evaluate: rotated functions need a rotation matrix");
+    if ((fn == PSSO_ELLIPSOID || fn == PSSO_ROT_ELLIPSOID) && !weights)
+        return bad(PSSO_ERR_ARG, "psso_evaluate: ellipsoid needs weights");
     if (precision != PSSO_PREC_F64 && precision != PSSO_PREC_F32_RECHECK)
         return bad(PSSO_ERR_ARG, "psso_evaluate: unknown precision");
     const bool f32 = precision == PSSO_PREC_F32_RECHECK;
@@ -99,10 +99,17 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
         w64[j] = weights ? weights[j] : 0.0;
         w32[j] = (float)w64[j];
     }
+    const bool rot = fn >= PSSO_ROT_ELLIPSOID;
+    const size_t nM = rot ? (size_t)D * D : 0;
+    std::vector<float> M32(nM);
+    for (size_t q = 0; q < nM; ++q) M32[q] = (float)rotation[q];
     char* dev = nullptr;
     const size_t nx = hx.size(), no = (size_t)Dp * 24, nf = (size_t)N * 16;
-    if (cudaMalloc(&dev, nx + 2 * no + nf + 1024) != cudaSuccess)
+    const size_t mbytes = ((nM * 12 + 255) / 256) * 256;
+    if (cudaMalloc(&dev, nx + 2 * no + nf + 1024 + mbytes) != cudaSuccess)
         return bad(PSSO_ERR_OOM, "psso_evaluate: cudaMalloc failed");
+    double* dM64 = reinterpret_cast<double*>(dev + nx + 2 * no + nf + 1024);
+    float* dM32 = reinterpret_cast<float*>(dM64 + nM);
     char* dX = dev;
     double* do64 = reinterpret_cast<double*>(dev + ((nx + 255) / 256) * 256);
     double* dw64 = do64 + Dp;
@@ -122,6 +129,11 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
             rc = bad(PSSO_ERR_CUDA, "psso_evaluate: upload failed");
             break;
         }
+        if (rot && (cudaMemcpyAsync(dM64, rotation, nM * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                    cudaMemcpyAsync(dM32, M32.data(), nM * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+            rc = bad(PSSO_ERR_CUDA, "psso_evaluate: upload failed");
+            break;
+        }
         InstDev in{};
         in.fn = fn;
         in.D = (int32_t)D;
@@ -133,6 +145,8 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
         in.o32 = do32;
         in.w64 = weights ? dw64 : nullptr;
         in.w32 = weights ? dw32 : nullptr;
+        in.M64 = rot ? dM64 : nullptr;
+        in.M32 = rot ? dM32 : nullptr;
         const int wpb = 8;
         const unsigned grid = (unsigned)((N + wpb - 1) / wpb);
         if (f32) evaluate_rows<true><<<grid, 32 * wpb, 0, s>>>(in, dX, N, df, derr);

@@ -57,11 +57,11 @@ enum Variant { V_F64_LAT64 = 0, V_F64_LAT32 = 1, V_F32R = 2 };
 
 struct HostInst {
     psso_problem pr;
-    std::vector<double> o, w;
+    std::vector<double> o, w, M;
     int G = 0, maxc = 0, nchunks = 0, Dp = 0, R = 1;
     size_t off_X = 0, off_P = 0, off_pf64 = 0, off_plo = 0, off_phi = 0, off_pver = 0,
            off_pflag = 0, off_grow = 0, off_rec = 0, off_rec2 = 0, off_gb = 0, off_gbrow = 0,
-           off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0;
+           off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0, off_M64 = 0, off_M32 = 0;
 };
 
 }  // namespace
@@ -113,8 +113,8 @@ psso_status check_problem(const psso_problem& pr, int precision, int idx)
 {
     const std::string at = "problem " + std::to_string(idx) + ": ";
     if (pr.fn < PSSO_SPHERE || pr.fn > PSSO_ROT_ACKLEY) return fail(PSSO_ERR_ARG, at + "unknown function id");
-    if (pr.fn >= PSSO_ROT_ELLIPSOID)
-        return fail(PSSO_ERR_UNSUPPORTED, at + "rotated functions are not available in this build");
+    if (pr.fn >= PSSO_ROT_ELLIPSOID && !pr.rotation)
+        return fail(PSSO_ERR_ARG, at + "rotated functions need a rotation matrix");
     if (pr.N < 1 || pr.N > 0x7fffffffLL) return fail(PSSO_ERR_ARG, at + "N must be in [1, 2^31-1]");
     if (pr.D < 1 || pr.D > 32 * MAX_CHUNKS_PER_LANE * 4) return fail(PSSO_ERR_ARG, at + "D must be in [1, 1024]");
     if (!std::isfinite(pr.lb) || !std::isfinite(pr.ub) || !(pr.lb < pr.ub))
@@ -132,6 +132,9 @@ psso_status check_problem(const psso_problem& pr, int precision, int idx)
     if (pr.shift)
         for (int64_t j = 0; j < pr.D; ++j)
             if (!std::isfinite(pr.shift[j])) return fail(PSSO_ERR_ARG, at + "shift must be finite");
+    if (pr.fn >= PSSO_ROT_ELLIPSOID)
+        for (int64_t q = 0; q < pr.D * pr.D; ++q)
+            if (!std::isfinite(pr.rotation[q])) return fail(PSSO_ERR_ARG, at + "rotation must be finite");
     if (precision == PSSO_PREC_F32_RECHECK) {
         if (pr.lattice != PSSO_LATTICE_F32)
             return fail(PSSO_ERR_ARG, at + "F32_RECHECK precision needs the F32 lattice");
@@ -354,6 +357,8 @@ void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
         d.o32 = reinterpret_cast<const float*>(A + I.off_o32);
         d.w64 = I.w.empty() ? nullptr : reinterpret_cast<const double*>(A + I.off_w64);
         d.w32 = I.w.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_w32);
+        d.M64 = I.M.empty() ? nullptr : reinterpret_cast<const double*>(A + I.off_M64);
+        d.M32 = I.M.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_M32);
         d.X = A + I.off_X;
         d.P = A + I.off_P;
         d.pf64 = reinterpret_cast<double*>(A + I.off_pf64);
@@ -455,6 +460,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.o.assign((size_t)I.pr.D, 0.0);
         if (I.pr.shift) std::copy(I.pr.shift, I.pr.shift + I.pr.D, I.o.begin());
         if (I.pr.weights) I.w.assign(I.pr.weights, I.pr.weights + I.pr.D);
+        if (I.pr.fn >= PSSO_ROT_ELLIPSOID) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
     }
     psso_status st = plan(h);
@@ -497,6 +503,8 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.off_o32 = take((size_t)I.Dp * 4);
         I.off_w64 = take(I.w.empty() ? 0 : (size_t)I.Dp * 8);
         I.off_w32 = take(I.w.empty() ? 0 : (size_t)I.Dp * 4);
+        I.off_M64 = take(I.M.size() * 8);
+        I.off_M32 = take(I.M.size() * 4);
     }
     h->arena_size = align_up(off, 256);
     cudaError_t e = cudaMalloc(&h->arena, h->arena_size);
@@ -551,6 +559,16 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_w64, w64, nd * 8, cudaMemcpyHostToDevice, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h->arena + I.off_w32, w32, nd * 4, cudaMemcpyHostToDevice, h->stream);
             h->h2d += (int64_t)(nd * 12);
+        }
+        if (!I.M.empty()) {
+            staging.emplace_back(I.M.size() * 4);
+            float* m32 = reinterpret_cast<float*>(staging.back().data());
+            for (size_t q = 0; q < I.M.size(); ++q) m32[q] = (float)I.M[q];
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->arena + I.off_M64, I.M.data(), I.M.size() * 8, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->arena + I.off_M32, m32, I.M.size() * 4, cudaMemcpyHostToDevice, h->stream);
+            h->h2d += (int64_t)(I.M.size() * 12);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -88,6 +88,8 @@ struct InstDev {
     const float* o32;
     const double* w64;            // ellipsoid weights or null
     const float* w32;
+    const double* M64;            // rotation [D][D] (rotated functions) or null
+    const float* M32;
     void* X;                      // positions  [N][Dp] (float or double)
     void* P;                      // pBests     [N][Dp]
     double* pf64;                 // pBest fitness in FP64 (F32 mode: valid iff pflag)

@@ -102,6 +102,8 @@ struct Hot {
     const float* o32;
     const double* w64;
     const float* w32;
+    const double* M64;   // rotation, row-major D x D (rotated functions only)
+    const float* M32;    // the same rounded to float
 };
 
 __device__ __forceinline__ Hot hot_of(const InstDev& d)
@@ -117,6 +119,7 @@ __device__ __forceinline__ Hot hot_of(const InstDev& d)
     h.S32 = d.S32; h.L32 = d.L32; h.lbf = d.lbf; h.ubf = d.ubf;
     h.lb = d.lb; h.ub = d.ub; h.span = d.span;
     h.o64 = d.o64; h.o32 = d.o32; h.w64 = d.w64; h.w32 = d.w32;
+    h.M64 = d.M64; h.M32 = d.M32;
     return h;
 }
 
@@ -169,11 +172,63 @@ __device__ __forceinline__ void fresh_chunk(double (&v)[4], uint32_t mask, uint3
 // chunks lane_g + 32 q).  Order: per-lane partials in ascending variable index
 // from +0.0, then an xor butterfly -- bit-identical to the oracle's 32-lane
 // order, since lanes beyond the group hold no variables (their partial is +0.0).
+__device__ __forceinline__ bool is_rotated(int fn) { return fn >= FN_ROT_ELLIPSOID; }
+// Function whose terms a rotated function applies to z = M (x - o).
+__device__ __forceinline__ int base_fn(int fn)
+{
+    return fn == FN_ROT_ELLIPSOID ? FN_ELLIPSOID
+         : fn == FN_ROT_RASTRIGIN ? FN_RASTRIGIN
+         : fn == FN_ROT_ACKLEY ? FN_ACKLEY : fn;
+}
+
+// z = M d, d = x - o, for the group's own variables (lane_g owns chunks
+// lane_g + 32 q): z_j = sum_k M_jk d_k with k ascending from +0.0 by fma, each
+// d_k broadcast from the lane that holds it -- the oracle's order.
+template <class Pos, int MAXC>
+__device__ __forceinline__ void rot_matvec64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g,
+                                             unsigned gmask, int G, double (&z)[MAXC][4])
+{
+    const int D = in.D;
+    double d[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * (lane_g + 32 * q) + m;
+            d[q][m] = (j < D) ? __dsub_rn((double)x[q][m], __ldg(in.o64 + j)) : 0.0;
+            z[q][m] = 0.0;
+        }
+#pragma unroll
+    for (int qk = 0; qk < MAXC; ++qk) {
+        for (int l = 0; l < G; ++l) {
+            if (128 * qk + 4 * l >= D) break;
+#pragma unroll
+            for (int mk = 0; mk < 4; ++mk) {
+                const int k = 128 * qk + 4 * l + mk;
+                const double dk = __shfl_sync(gmask, d[qk][mk], l, G);
+                if (k < D) {
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int j = 4 * (lane_g + 32 * q) + m;
+                            if (j < D) z[q][m] = __fma_rn(__ldg(in.M64 + (size_t)j * D + k), dk, z[q][m]);
+                        }
+                }
+            }
+        }
+    }
+}
+
 template <class Pos, int MAXC>
 __device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
                         int G)
 {
-    const int D = in.D, fn = in.fn, nch = in.nchunks;
+    const int D = in.D, nch = in.nchunks;
+    const bool rot = is_rotated(in.fn);
+    const int fn = base_fn(in.fn);
+    double zr[MAXC][4];
+    if (rot) rot_matvec64<Pos, MAXC>(in, x, lane_g, gmask, G, zr);
     double acc = 0.0, acc2 = 0.0;
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
@@ -196,7 +251,7 @@ __device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], 
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int j = 4 * c + m;
-                dv[m] = (j < D) ? __dsub_rn((double)x[q][m], __ldg(in.o64 + j)) : 0.0;
+                dv[m] = rot ? zr[q][m] : (j < D) ? __dsub_rn((double)x[q][m], __ldg(in.o64 + j)) : 0.0;
             }
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -263,12 +318,85 @@ struct Fit32 {
     float f, E;
 };
 
+// FP32 z = M d with a running bound: z~_j by fma in FP32 with M rounded to
+// float and d~ = fl(x - o), summed in blocks of 32 terms (each block from 0,
+// then added to z~_j), and ez_j >= |z~_j - z_j| from S_j = sum |M~_jk||d~_k|:
+// |z~ - z| <= (gamma_32 + gamma_nb + 2u) S (1 + O(u)), nb = number of blocks --
+// the fma chains, the block sums, M's rounding and d's rounding.
+template <int MAXC>
+__device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAXC][4], int lane_g,
+                                             unsigned gmask, int G, float (&z)[MAXC][4],
+                                             float (&ez)[MAXC][4])
+{
+    const int D = in.D;
+    float d[MAXC][4], t[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * (lane_g + 32 * q) + m;
+            d[q][m] = (j < D) ? __fsub_rn(x[q][m], __ldg(in.o32 + j)) : 0.f;
+            z[q][m] = 0.f;
+            t[q][m] = 0.f;
+            ez[q][m] = 0.f;
+        }
+#pragma unroll
+    for (int qk = 0; qk < MAXC; ++qk) {
+        for (int l = 0; l < G; ++l) {
+            if (128 * qk + 4 * l >= D) break;
+#pragma unroll
+            for (int mk = 0; mk < 4; ++mk) {
+                const int k = 128 * qk + 4 * l + mk;
+                const float dk = __shfl_sync(gmask, d[qk][mk], l, G);
+                if (k < D) {
+                    const float adk = fabsf(dk);
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int j = 4 * (lane_g + 32 * q) + m;
+                            if (j < D) {
+                                const float mjk = __ldg(in.M32 + (size_t)j * D + k);
+                                t[q][m] = __fmaf_rn(mjk, dk, t[q][m]);
+                                ez[q][m] = __fmaf_rn(fabsf(mjk), adk, ez[q][m]);
+                            }
+                        }
+                }
+            }
+            if ((l & 7) == 7) {   // close a block of 32 terms
+#pragma unroll
+                for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        z[q][m] = __fadd_rn(z[q][m], t[q][m]);
+                        t[q][m] = 0.f;
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) z[q][m] = __fadd_rn(z[q][m], t[q][m]);
+    const int nb = (D + 31) / 32;
+    const float c = 1.02f * (float)(32 + nb + 3) * U32;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ez[q][m] = c * ez[q][m] * (1.f + (float)D * U32);
+}
+
 template <int MAXC>
 __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
                        int G)
 {
-    const int D = in.D, fn = in.fn, nch = in.nchunks;
+    const int D = in.D, nch = in.nchunks;
+    const bool rot = is_rotated(in.fn);
+    const int fn = base_fn(in.fn);
+    float zr[MAXC][4], ezr[MAXC][4];
+    if (rot) rot_matvec32<MAXC>(in, x, lane_g, gmask, G, zr, ezr);
     float acc = 0.f, acc2 = 0.f, accE = 0.f, accZ = 0.f;
+    float rS1 = 0.f, rQ = 0.f;   // rotated: absolute error bounds of S1 and Q (Ackley)
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
         const int c = lane_g + 32 * q;
@@ -289,7 +417,7 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int j = 4 * c + m;
-                dv[m] = (j < D) ? __fsub_rn(x[q][m], __ldg(in.o32 + j)) : 0.f;
+                dv[m] = rot ? zr[q][m] : (j < D) ? __fsub_rn(x[q][m], __ldg(in.o32 + j)) : 0.f;
             }
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -300,12 +428,26 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
                 case FN_SPHERE:
                     acc = __fadd_rn(acc, __fmul_rn(z, z));
                     break;
-                case FN_ELLIPSOID:
-                    acc = __fadd_rn(acc, __fmul_rn(__ldg(in.w32 + j), __fmul_rn(z, z)));
+                case FN_ELLIPSOID: {
+                    const float wj = __ldg(in.w32 + j);
+                    const float t = __fmul_rn(wj, __fmul_rn(z, z));
+                    acc = __fadd_rn(acc, t);
+                    if (rot) {   // z~ has error ez: w (2|z~| + ez) ez, plus the products' roundings
+                        const float ez = ezr[q][m];
+                        accE = __fadd_rn(accE, 4.2f * U32 * t + 1.01f * wj * (2.f * fabsf(z) + ez) * ez);
+                    }
                     break;
+                }
                 case FN_RASTRIGIN: {
                     const float s = sinpi_reduced_f32(__fsub_rn(z, rintf(z)));
-                    acc = __fadd_rn(acc, __fmaf_rn(z, z, __fmul_rn(20.f, __fmul_rn(s, s))));
+                    const float t = __fmaf_rn(z, z, __fmul_rn(20.f, __fmul_rn(s, s)));
+                    acc = __fadd_rn(acc, t);
+                    if (rot) {   // |t'(xi)| <= 2|xi| + 20 pi min(1, 2 pi |xi|), |xi| <= |z~| + ez
+                        const float ez = ezr[q][m];
+                        const float xi = fabsf(z) + ez;
+                        accE = __fadd_rn(accE, (2.f * SINPI32_ERR_U + 4.f) * U32 * t +
+                                                   1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ez);
+                    }
                     break;
                 }
                 case FN_ROSENBROCK:
@@ -340,6 +482,12 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
                     const float s = sinpi_reduced_f32(__fsub_rn(z, rintf(z)));
                     acc2 = __fadd_rn(acc2, __fmul_rn(s, s));
                     accZ = __fadd_rn(accZ, fabsf(z));
+                    if (rot) {   // |d z^2| <= (2|z~| + ez) ez, |d sin^2(pi z)| <= pi min(1, 2 pi |xi|) ez
+                        const float ez = ezr[q][m];
+                        const float xi = fabsf(z) + ez;
+                        rS1 = __fadd_rn(rS1, 1.01f * (2.f * fabsf(z) + ez) * ez);
+                        rQ = __fadd_rn(rQ, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ez);
+                    }
                     break;
                 }
                 default:
@@ -359,11 +507,23 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
         break;
     case FN_ELLIPSOID:
         r.f = acc;
-        r.E = 1.1f * (5.2f + csum) * U32 * acc;
+        if (rot) {
+            for (int off = G >> 1; off > 0; off >>= 1)
+                accE = __fadd_rn(accE, __shfl_xor_sync(gmask, accE, off, G));
+            r.E = 1.1f * (accE + csum * U32 * acc);
+        } else {
+            r.E = 1.1f * (5.2f + csum) * U32 * acc;
+        }
         break;
     case FN_RASTRIGIN:
         r.f = acc;
-        r.E = 1.1f * (2.f * SINPI32_ERR_U + 3.f + 16.1f + 1.f + csum) * U32 * acc;
+        if (rot) {
+            for (int off = G >> 1; off > 0; off >>= 1)
+                accE = __fadd_rn(accE, __shfl_xor_sync(gmask, accE, off, G));
+            r.E = 1.1f * (accE + csum * U32 * acc);
+        } else {
+            r.E = 1.1f * (2.f * SINPI32_ERR_U + 3.f + 16.1f + 1.f + csum) * U32 * acc;
+        }
         break;
     case FN_ROSENBROCK:
         for (int off = G >> 1; off > 0; off >>= 1)
@@ -382,11 +542,26 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
         const float C = expm1_f32(__fmul_rn(-2.f, __fdiv_rn(acc2, Df)));
         const float f1 = __fmul_rn(-20.f, B), f2 = __fmul_rn(-0x1.5bf0a8p+1f, C);
         r.f = __fadd_rn(f1, f2);
-        const float relS = (3.1f + csum) * U32;
-        const float EQ = 1.01f * 3.14159275f * U32 * accZ +
-                         (2.f * SINPI32_ERR_U + 1.f + csum) * U32 * acc2;
-        r.E = 1.1f * (0.5f * relS * f1 + (EXPM1F_ERR_U + 6.f) * U32 * f1 +
-                      (2.f * 2.7182818f / Df) * EQ + (EXPM1F_ERR_U + 8.f) * U32 * f2 + U32 * r.f);
+        if (!rot) {
+            const float relS = (3.1f + csum) * U32;
+            const float EQ = 1.01f * 3.14159275f * U32 * accZ +
+                             (2.f * SINPI32_ERR_U + 1.f + csum) * U32 * acc2;
+            r.E = 1.1f * (0.5f * relS * f1 + (EXPM1F_ERR_U + 6.f) * U32 * f1 +
+                          (2.f * 2.7182818f / Df) * EQ + (EXPM1F_ERR_U + 8.f) * U32 * f2 + U32 * r.f);
+        } else {
+            for (int off = G >> 1; off > 0; off >>= 1) {
+                rS1 = __fadd_rn(rS1, __shfl_xor_sync(gmask, rS1, off, G));
+                rQ = __fadd_rn(rQ, __shfl_xor_sync(gmask, rQ, off, G));
+            }
+            // absolute bounds on S1 and Q; f1 = -20 expm1(-0.2 sqrt(S1/D)) changes by at most
+            // 4 sqrt(dS1 / D) (sqrt is 1/2-Hoelder), or, when dS1 <= S1 / 2, by
+            // 1.5 f1 dS1 / S1 (|df1/dS1| <= f1 / (2 S1), f1 concave with f1(0) = 0)
+            const float ES = rS1 + (3.1f + csum) * U32 * acc;
+            const float EQ = rQ + (2.f * SINPI32_ERR_U + 1.f + csum) * U32 * acc2;
+            const float d1 = (ES <= 0.5f * acc) ? 1.5f * f1 * ES / acc : 4.f * __fsqrt_ru(ES / Df);
+            r.E = 1.1f * (d1 + (EXPM1F_ERR_U + 6.f) * U32 * f1 + (2.f * 2.7182818f / Df) * EQ +
+                          (EXPM1F_ERR_U + 8.f) * U32 * f2 + U32 * r.f);
+        }
         acc = r.f;
         break;
     }

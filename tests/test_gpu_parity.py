@@ -59,9 +59,11 @@ def test_sphere_d30_full_run_bitexact(lib):
 
 
 CASES = [(37, 5, 30), (130, 129, 8), (9, 257, 5), (64, 1, 25), (33, 31, 20), (5, 1000, 2)]
+ALL_FNS = ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley", "rot_ellipsoid",
+           "rot_rastrigin", "rot_ackley"]
 
 
-@pytest.mark.parametrize("fn", ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley"])
+@pytest.mark.parametrize("fn", ALL_FNS)
 @pytest.mark.parametrize("lattice", ["f64", "f32"])
 @pytest.mark.parametrize("N,D,t", CASES)
 def test_fp64_bitexact(lib, fn, lattice, N, D, t):
@@ -132,7 +134,7 @@ def _assert_same_decisions(g, r, t, fn):
     lo = log["value_lo"].astype(np.float64)
     hi = log["value_hi"].astype(np.float64)
     assert np.all(lo <= r["log_v"]) and np.all(r["log_v"] <= hi)
-    floor = 1e-6 * (20 + np.e) if fn == "ackley" else 0.0
+    floor = 1e-6 * (20 + np.e) if fn.endswith("ackley") else 0.0
     scale = np.maximum(np.abs(r["pF"]), floor)
     rel = np.abs(g["pF"] - r["pF"]) / np.where(scale > 0, scale, 1.0)
     assert np.all(rel <= 1e-6), rel.max()
@@ -140,7 +142,7 @@ def _assert_same_decisions(g, r, t, fn):
     assert b == r["log_b"][t] and v == r["log_v"][t]
 
 
-@pytest.mark.parametrize("fn", ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley"])
+@pytest.mark.parametrize("fn", ALL_FNS)
 @pytest.mark.parametrize("N,D,t", [(61, 13, 40), (300, 100, 30), (8, 700, 6)])
 def test_fp32_recheck_same_decisions(lib, fn, N, D, t):
     p = workload.problem(fn, N, D, seed=21 + D, lattice="f32")
@@ -160,18 +162,19 @@ def test_fp32_recheck_multiblock(lib, cfg):
 
 def test_evaluate_fp64_matches_oracle(lib):
     rng = np.random.default_rng(0)
-    for fn in ("sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley"):
+    for fn in ALL_FNS:
         for D in (1, 7, 100, 333):
             lb, ub = workload.BOUNDS[fn]
             X = rng.uniform(lb, ub, (17, D))
             o = workload.shift(D, 0.8 * lb, 0.8 * ub, 9)
             w = workload.ellipsoid_weights(D)
-            f, _ = lib.psso_evaluate(fn, X, o, w)
-            ref = np.array([oracle.fitness(fn, x, o, w) for x in X])
+            M = workload.rotation(D, 4) if fn.startswith("rot_") else None
+            f, _ = lib.psso_evaluate(fn, X, o, w, M)
+            ref = np.array([oracle.fitness(fn, x, o, w, M) for x in X])
             assert np.array_equal(f, ref), (fn, D)
 
 
-@pytest.mark.parametrize("fn", ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley"])
+@pytest.mark.parametrize("fn", ALL_FNS)
 def test_evaluate_fp32_error_bound(lib, fn):
     """|f32 - f64| <= err on random rows and on rows built to stress the
     bound (near-integer and near-half-integer z, tiny z, mixed magnitudes)."""
@@ -181,21 +184,28 @@ def test_evaluate_fp32_error_bound(lib, fn):
     for D in (1, 3, 64, 257, 1000):
         o = workload.shift(D, 0.8 * lb, 0.8 * ub, 5, lattice="f32")
         w = workload.ellipsoid_weights(D)
+        M = workload.rotation(D, 6) if fn.startswith("rot_") else None
         rows = [rng.uniform(lb, ub, (64, D))]
         k = rng.integers(-3, 4, (64, D)).astype(np.float64)
         rows.append(o + k + rng.normal(0, 1e-3, (64, D)))
         rows.append(o + k + 0.5 + rng.normal(0, 1e-3, (64, D)))
         rows.append(o + rng.normal(0, 1e-4, (64, D)))
         X = np.clip(np.concatenate(rows), lb, ub).astype(np.float32).astype(np.float64)
-        f32, err = lib.psso_evaluate(fn, X, o, w, precision="f32")
-        f64, _ = lib.psso_evaluate(fn, X, o, w, precision="f64")
+        f32, err = lib.psso_evaluate(fn, X, o, w, M, precision="f32")
+        f64, _ = lib.psso_evaluate(fn, X, o, w, M, precision="f64")
         assert np.all(np.abs(f32 - f64) <= err), (fn, D)
-        floor = 1e-6 * (20 + np.e) if fn == "ackley" else 1e-300
-        worst_rel = max(worst_rel, float(np.max(np.abs(f32 - f64) / np.maximum(np.abs(f64), floor))))
-        # the bound is rigorous but should not be vacuous: within ~1e-4 relative
-        assert np.all(err <= 1e-4 * np.maximum(np.abs(f64), floor) + 1e-30), (fn, D)
+        floor = 1e-6 * (20 + np.e) if fn.endswith("ackley") else 1e-300
+        rel = np.abs(f32 - f64) / np.maximum(np.abs(f64), floor)
+        worst_rel = max(worst_rel, float(np.max(rel)))
+        # the bound is rigorous but should not be vacuous.  Rotated functions: the
+        # error of z_j = sum_k M_jk d_k scales with sum |M_jk||d_k|, so near the
+        # optimum, where z cancels, any bound looks loose relative to f; check
+        # those on the uniformly random rows.
+        loose = 1e-4 if M is None else 5e-5 * (32 + D / 32) + 1e-4
+        sel = slice(None) if M is None else slice(0, 64)
+        assert np.all(err[sel] <= loose * np.maximum(np.abs(f64[sel]), floor) + 1e-30), (fn, D)
     print(f"{fn}: worst |f32 - f64| / |f64| = {worst_rel:.3e}")
-    assert worst_rel <= 1e-6, worst_rel
+    assert worst_rel <= (1e-6 if not fn.startswith("rot_") else 1e-5), worst_rel
 
 
 def test_timeout_is_reported_not_hung(lib):
