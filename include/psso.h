@@ -264,6 +264,45 @@ psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, const double
                                   const double* shift, const double* weights, int32_t precision,
                                   double* f, double* err, void* stream);
 
+/* Differentiable batched fitness in FP32 (the fitness of Kernel Function (E),
+ * Sec. 2.3.2, and its gradient; the paper names gradient descent in the title
+ * of Sec. 2 only, so these calls have no counterpart in its method).
+ *
+ * DEVICE pointers, all float32, row-major and unpadded: X (N*D), shift (D),
+ * weights (D; ELLIPSOID / ROT_ELLIPSOID only, else may be NULL), rotation
+ * (D*D, M[j*D + k] for z_j = sum_k M_jk (x_k - o_k); rotated functions only).
+ *   psso_fitness_forward:  f (N) = f(X_i) in FP32 (relative error a few 2^-24
+ *                          for well-conditioned sums; not the bit pattern of
+ *                          psso_evaluate).
+ *   psso_fitness_backward: grad_X (N*D) = grad_f[i] * df/dx (X_i); for rotated
+ *                          functions df/dx = M^T df/dz.
+ * Gradients (z the function's coordinates):
+ *   sphere 2 z_j;  ellipsoid 2 w_j z_j;  Rastrigin 2 z_j + 20 pi sin(2 pi z_j);
+ *   Rosenbrock [j<D-1](2 z_j - 400 a_j u_j) + [j>0] 200 u_{j-1},
+ *     a = z + 1, u_j = a_{j+1} - a_j^2;
+ *   Ackley 4 e^{-0.2 A} z_j / (A D) + 2 pi e^{C} sin(2 pi z_j) / D,
+ *     A = sqrt(sum z^2 / D), C = sum cos(2 pi z) / D  (the first term is 0 at A = 0).
+ * 1 <= D <= 1024; otherwise, or for a NULL pointer the function needs,
+ * PSSO_ERR_ARG.  Work is enqueued on `stream` (cudaStream_t, NULL = default);
+ * the calls allocate nothing and return without waiting. */
+psso_status psso_fitness_forward(psso_fn fn, int64_t N, int64_t D, const float* X, const float* shift,
+                                 const float* weights, const float* rotation, float* f, void* stream);
+psso_status psso_fitness_backward(psso_fn fn, int64_t N, int64_t D, const float* X, const float* shift,
+                                  const float* weights, const float* rotation, const float* grad_f,
+                                  float* grad_X, void* stream);
+
+/* gBest polish (an optional local search; the paper has no counterpart and
+ * psso_run never calls it): from instance k's gBest row, `steps` FP32 steps
+ * x <- clamp(x - lr df/dx, [lb, ub]) with the gradient of
+ * psso_fitness_backward.  The polished row replaces the gBest particle's pBest
+ * (and the gBest) only if its FP64 fitness is strictly lower; the particle's
+ * position x is untouched.  A run that never calls psso_polish is unaffected;
+ * one that does leaves the oracle's trajectory.  *improved (may be NULL) is
+ * set to 1 when the row was replaced, else 0.  Synchronises the handle's
+ * stream.  PSSO_ERR_ARG for a bad instance, steps < 0 or lr not a finite
+ * value >= 0. */
+psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double lr, int32_t* improved);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);
 

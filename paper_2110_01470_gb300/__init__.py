@@ -120,6 +120,14 @@ def load(path: str = LIB_PATH):
         "psso_evaluate_noalloc": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_fitness_forward": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_fitness_backward": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_polish": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                         ctypes.POINTER(ctypes.c_int32)], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -286,6 +294,34 @@ def psso_evaluate_noalloc(fn, N, D, X_ptr, shift_ptr, weights_ptr, precision, f_
         precision = PRECISION[precision]
     _check(load().psso_evaluate_noalloc(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
                                         int(precision), f_ptr, err_ptr, stream))
+
+
+def psso_fitness_forward(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr, f_ptr,
+                         stream=None):
+    """FP32 batched fitness on device buffers (raw float32 device pointers).
+    Enqueued on ``stream``; does not wait."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    _check(load().psso_fitness_forward(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
+                                       rotation_ptr, f_ptr, stream))
+
+
+def psso_fitness_backward(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr, grad_f_ptr,
+                          grad_X_ptr, stream=None):
+    """grad_X = grad_f[:, None] * df/dX on device buffers (raw float32 device
+    pointers).  Enqueued on ``stream``; does not wait."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    _check(load().psso_fitness_backward(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
+                                        rotation_ptr, grad_f_ptr, grad_X_ptr, stream))
+
+
+def psso_polish(h, instance=0, steps=20, lr=1e-3):
+    """Gradient polish of the gBest row of ``instance``; returns True when it
+    replaced the gBest particle's pBest (strictly lower FP64 fitness)."""
+    improved = ctypes.c_int32(0)
+    _check(load().psso_polish(h, int(instance), int(steps), float(lr), ctypes.byref(improved)))
+    return bool(improved.value)
 
 
 def psso_last_error():

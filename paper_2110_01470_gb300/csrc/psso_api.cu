@@ -760,6 +760,32 @@ psso_status psso_stats(psso_handle h, psso_stats_t* out)
     return PSSO_OK;
 }
 
+psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double lr, int32_t* improved)
+{
+    if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    if (steps < 0 || !(lr >= 0.0) || !std::isfinite(lr)) return fail(PSSO_ERR_ARG, "need steps >= 0 and a finite lr >= 0");
+    if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier");
+    psso_status st = read_status(h);
+    if (st != PSSO_OK) return st;
+    const HostInst& I = h->inst[instance];
+    GBestDev before;
+    CUDA_TRY(cudaMemcpy(&before, h->arena + I.off_gb, sizeof before, cudaMemcpyDeviceToHost));
+    int owner = -1;
+    if (I.R > 1)
+        for (const auto& u : h->units)
+            if (u.inst == instance && before.idx >= u.i0 && before.idx < u.i1) owner = u.rank;
+    CUDA_TRY(launch_polish(reinterpret_cast<const InstDev*>(h->arena + h->off_instdev), instance, h->lattice,
+                           owner, h->gen, steps, (float)lr, h->stream));
+    GBestDev after;
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    CUDA_TRY(cudaMemcpy(&after, h->arena + I.off_gb, sizeof after, cudaMemcpyDeviceToHost));
+    // The kernel only ever replaces the gBest by a row with a strictly lower FP64
+    // value (and then always records that value).
+    if (improved) *improved = (after.has64 && (!before.has64 || after.f64 < before.f64)) ? 1 : 0;
+    return PSSO_OK;
+}
+
 struct SaveHeader {
     char magic[8];
     int64_t gen, evals, updates, state_bytes;

@@ -147,6 +147,9 @@ cudaError_t gen_call(int variant, int op, int mc_index, const KParams* p, int gr
                      size_t smem, cudaStream_t s, int* out);
 cudaError_t launch_best_f64(const InstDev* inst, int n_inst, int lattice, cudaStream_t s);
 
+cudaError_t launch_polish(const InstDev* inst, int k, int lattice, int owner_rank, int64_t g, int steps,
+                          float lr, cudaStream_t s);
+
 // Records the calling thread's last error message (psso_last_error).
 void set_last_error(const char* msg);
 
