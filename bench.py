@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--threads-per-block", type=int, default=0)
+    ap.add_argument("--polish-steps", type=int, default=2,
+                    help="timed runs with the gBest polish (workloads that define one)")
     return ap.parse_args()
 
 
@@ -75,9 +77,12 @@ FIT32_OPS = {"sphere": 3, "ellipsoid": 4, "rastrigin": 17, "rosenbrock": 9, "ack
 def alu_ops_per_update(p):
     """Algorithmic 32-bit ALU operations per particle-variable update: Philox
     (10 rounds x 8 ops), Eq. 2.1 selection (3 compares + select), the fresh-value
-    map (4 ops at rate 1 - Cw), and the FP32 fitness term."""
+    map (4 ops at rate 1 - Cw), and the FP32 fitness term; a rotated function
+    adds its row of z = M (x - o): D fused multiply-adds per variable."""
+    base = p["fn"].replace("rot_", "")
+    rot = p["D"] if p["fn"].startswith("rot_") else 0
     return (80.0 * philox_blocks_per_update(p) + 4.0 + 4.0 * (1.0 - p["Cw"])
-            + FIT32_OPS[p["fn"]])
+            + FIT32_OPS[base] + rot)
 
 
 # ---------------------------------------------------------------------------
@@ -205,6 +210,99 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def psso_best_values(psso, problems, prec, t, sptr):
+    """gBest value of every instance after one plain run of t generations."""
+    h = psso.psso_create_ex(problems, prec, stream=sptr)
+    try:
+        psso.psso_run(h, t)
+        return [psso.psso_best(h, k)[0] for k in range(len(problems))]
+    finally:
+        psso.psso_destroy(h)
+
+
+def polish_arm(psso, torch, problems, prec, t, pol, sptr, stream, steps, flush):
+    """SSO with the gBest polish every K generations (each instance), timed
+    with the polish inside the timed region (it synchronises, so the time is
+    host wall-clock around device-synchronised steps)."""
+    K, n_steps, lr = int(pol["K"]), int(pol["steps"]), float(pol["lr"])
+    h = psso.psso_create_ex(problems, prec, stream=sptr)
+    times, improved = [], 0
+    try:
+        for s in range(steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            psso.psso_reset(h)
+            done, imp = 0, 0
+            while done < t:
+                c = min(K, t - done)
+                psso.psso_run(h, c)
+                done += c
+                if done % K == 0:
+                    for k in range(len(problems)):
+                        imp += psso.psso_polish(h, k, n_steps, lr)
+            psso.psso_sync(h)
+            if s > 0:                   # the first pass is the warm-up
+                times.append(time.perf_counter() - t0)
+                improved = imp
+        on = [psso.psso_best(h, k)[0] for k in range(len(problems))]
+    finally:
+        psso.psso_destroy(h)
+    upd = sum(p["N"] * p["D"] for p in problems) * t
+    return {"K": K, "steps": n_steps, "lr": lr, "ms_per_step": 1e3 * sum(times) / len(times),
+            "value": upd * len(times) / sum(times), "unit": UNIT,
+            "polishes_per_step": (t // K) * len(problems), "improved_per_step": improved,
+            "gbest_on": on}
+
+
+def grad_arm(psso, torch, problems, stream, flush, reps=20):
+    """FP32 forward and backward fitness kernels on N random rows per
+    problem: device time per call (CUDA events, L2 flushed before each) and
+    throughput against the HBM copy peak (bytes: forward reads X, backward
+    reads X and writes grad_X; the row-vector and M reads are not counted)."""
+    out = []
+    for p in problems:
+        N, D = p["N"], p["D"]
+        g = torch.Generator(device="cuda").manual_seed(7)
+        X = (torch.rand((N, D), generator=g, device="cuda") * (p["ub"] - p["lb"]) + p["lb"])
+        o = torch.tensor(p["o"], dtype=torch.float32, device="cuda")
+        w = None if p["w"] is None else torch.tensor(p["w"], dtype=torch.float32, device="cuda")
+        M = None if p["M"] is None else torch.tensor(p["M"], dtype=torch.float32, device="cuda")
+        f = torch.empty(N, device="cuda")
+        gf = torch.ones(N, device="cuda")
+        gX = torch.empty_like(X)
+        ptr = lambda a: None if a is None else a.data_ptr()
+        sp = stream.cuda_stream
+
+        def fwd():
+            psso.psso_fitness_forward(p["fn"], N, D, X.data_ptr(), o.data_ptr(), ptr(w), ptr(M),
+                                      f.data_ptr(), sp)
+
+        def bwd():
+            psso.psso_fitness_backward(p["fn"], N, D, X.data_ptr(), o.data_ptr(), ptr(w), ptr(M),
+                                       gf.data_ptr(), gX.data_ptr(), sp)
+
+        res = {"fn": p["fn"], "N": N, "D": D}
+        for name, call, nbytes in (("forward", fwd, 4 * N * D), ("backward", bwd, 8 * N * D)):
+            call()
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            m = statistics.median(ms)
+            res[name] = {"ms": m, "rows_per_s": N / (m / 1e3), "gbs": nbytes / (m / 1e3) / 1e9}
+            if p["fn"].startswith("rot_"):
+                mult = 1 if name == "forward" else 2
+                res[name]["fp32_tflops"] = mult * 2.0 * N * D * D / (m / 1e3) / 1e12
+        out.append(res)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -291,6 +389,16 @@ def main():
                 "kernel_ms": sum(k64) / len(k64), "speedup_f32_over_f64": value / world / v64,
                 "same_gbest": bool(b64[1] == best[1] and b64[0] == best[0])}
 
+    # --- opt-in gBest polish (workloads that name one) -------------------------------------
+    polish = None
+    if cfg.get("polish") and args.polish_steps > 0:
+        polish = polish_arm(psso, torch, problems, prec, t, cfg["polish"], sptr, stream,
+                            args.polish_steps, flush)
+        polish["gbest_off"] = psso_best_values(psso, problems, prec, t, sptr)
+    grad = None
+    if cfg.get("polish"):
+        grad = grad_arm(psso, torch, problems, stream, flush)
+
     # --- end to end through the public API with host buffers ------------------------------
     e2e_t, h2d, d2h = [], 0, 0
     for k in range(args.e2e_steps + 1):
@@ -310,7 +418,7 @@ def main():
 
     # --- roofline of the persistent generation kernel ------------------------------------
     p0 = problems[0]
-    ops = alu_ops_per_update(p0) * upd_per_step / len(problems) * len(problems)
+    ops = sum(alu_ops_per_update(p) * p["N"] * p["D"] * t for p in problems)
     kernel_s = (sum(kern_ms) / len(kern_ms)) / 1e3
     peak = SM_COUNT * LANES_PER_SM * ALU_CLOCK_MHZ * 1e6 / 1e12     # T ops / s
     achieved = ops / kernel_s / 1e12
@@ -318,7 +426,7 @@ def main():
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "sso_generations<float, true>" if prec == "f32" else
                           "sso_generations<..., false>",
-                "ops_per_update": alu_ops_per_update(p0),
+                "ops_per_update": ops / upd_per_step,
                 "kernel_ms_per_launch": kernel_s * 1e3,
                 "peak_note": "152 SMs x 128 lanes x 2070 MHz (derived, not measured)"}
 
@@ -347,6 +455,10 @@ def main():
         "roofline": roofline,
         "clocks": clk.summary(),
     }
+    if polish is not None:
+        line["polish"] = polish
+    if grad is not None:
+        line["fitness_grad"] = grad
     if world == 1 or rank == 0:
         line["cpu_baseline"] = cpu_baseline(problems, t, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -121,5 +121,5 @@ def config(name: str):
         return dict(problems=batched_table(512, seed=1), t=1000, precision="f32")
     if name == "grad_d256":
         ps = [problem(f, 4096, 256, seed=1, lattice="f32") for f in ("rosenbrock", "rot_ackley")]
-        return dict(problems=ps, t=3000, precision="f32")
+        return dict(problems=ps, t=3000, precision="f32", polish=dict(K=50, steps=20, lr=1e-3))
     raise KeyError(name)
