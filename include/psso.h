@@ -303,6 +303,22 @@ psso_status psso_fitness_backward(psso_fn fn, int64_t N, int64_t D, const float*
  * value >= 0. */
 psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double lr, int32_t* improved);
 
+/* Rotation z = M (x - o) of N rows on the tensor cores (the transform of the
+ * rotated test functions; the paper's functions are unrotated, the rotated
+ * forms follow the usual z = M (x - o) convention).  DEVICE pointers, float32,
+ * row-major: X (N*D), shift (D), rotation (D*D, M[j*D + k]), Z (N*D, out).
+ * d = fl32(x - o) and M are split exactly into three BF16 parts each; the six
+ * products above 2^-24 are accumulated in FP32 by tcgen05 MMAs (main part and
+ * corrections in separate accumulators) and added.  Error model:
+ * |z~_j - sum_k M_jk d_k| <= c(Kp) * sum_k |M_jk| |d_k| + 2^-24 |z~_j|,
+ * Kp = D rounded up to 64, c(Kp) = 1.05 (2^-22 1.04 (Kp/16)(1 + 5 2^-7)
+ * + 1.03 2^-23 + 2.02 2^-24) when every MMA instruction errs by at most 2^-22
+ * of its operand magnitudes.  1 <= N <= 2^24, 1 <= D <= 8192.  Allocates its
+ * operand planes for the call and synchronises `stream`.  PSSO_ERR_TIMEOUT if
+ * a pipeline wait ran out (the device is left usable). */
+psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift, const float* rotation,
+                        float* Z, void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);
 

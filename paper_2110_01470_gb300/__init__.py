@@ -126,6 +126,8 @@ def load(path: str = LIB_PATH):
         "psso_fitness_backward": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_rotate": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
         "psso_polish": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                          ctypes.POINTER(ctypes.c_int32)], st),
         "psso_last_error": ([], ctypes.c_char_p),
@@ -314,6 +316,12 @@ def psso_fitness_backward(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr,
         fn = FN[fn]
     _check(load().psso_fitness_backward(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
                                         rotation_ptr, grad_f_ptr, grad_X_ptr, stream))
+
+
+def psso_rotate(N, D, X_ptr, shift_ptr, rotation_ptr, Z_ptr, stream=None):
+    """Z = (X - o) M^T on the tensor cores (raw float32 device pointers).
+    Synchronises ``stream``."""
+    _check(load().psso_rotate(int(N), int(D), X_ptr, shift_ptr, rotation_ptr, Z_ptr, stream))
 
 
 def psso_polish(h, instance=0, steps=20, lr=1e-3):
