@@ -137,6 +137,11 @@ typedef struct {
                                    uses a control warp that exchanges gBest while
                                    the other warps compute the next generation;
                                    2 = never                                        */
+    int32_t tensor_rotation;    /* rotated functions with F32_RECHECK precision:
+                                   0 = auto (swarms with N >= 128 and D >= 32 run
+                                   each generation as a kernel sequence around a
+                                   tcgen05 tensor-core GEMM for z = M (x - o));
+                                   1 = always; -1 = never (per-particle kernel)     */
 } psso_config;
 
 /* One log entry (psso_get_log). */

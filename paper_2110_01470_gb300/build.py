@@ -1,7 +1,8 @@
 """Builds ``libpsso.so`` (the CUDA library behind include/psso.h) in-tree.
 
 Every ``csrc/*.cu`` translation unit is compiled by nvcc for sm_103a in
-parallel, then linked into one shared library next to this file.  Usage:
+parallel (``gen_variant.cu`` once per kernel variant and width), then linked
+into one shared library next to this file.  Usage:
 ``python -m paper_2110_01470_gb300.build`` or ``build_library()``.
 """
 from __future__ import annotations
@@ -42,21 +43,29 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    variant_src = os.path.join(CSRC, "gen_variant.cu")
+    jobs = [(src, os.path.basename(src)[:-3], [])
+            for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))) if src != variant_src]
+    # the persistent kernel: one object per (variant, width), compiled in parallel
+    jobs += [(variant_src, f"gen_variant_{v}_{m}", [f"-DPSSO_VARIANT={v}", f"-DPSSO_MC={m}"])
+             for v in range(3) for m in (1, 2, 4, 8)]
+    # longest first
+    jobs.sort(key=lambda j: (j[0] != variant_src, -int(j[1][-1]) if j[0] == variant_src else 0))
     exe = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, name, defs = job
+        obj = os.path.join(OBJDIR, name + ".o")
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{p.stderr}")
+            raise RuntimeError(f"nvcc failed on {name}:\n{p.stderr}")
         if verbose and p.stderr:
             sys.stderr.write(p.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(compile_one, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs]
     p = subprocess.run(cmd, capture_output=True, text=True)

@@ -4,18 +4,24 @@
 
 namespace psso {
 
-cudaError_t gen_f64_lat64(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
-cudaError_t gen_f64_lat32(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
-cudaError_t gen_f32r(int, int, const KParams*, int, int, size_t, cudaStream_t, int*);
+// One entry per (variant, width), each in its own object built from gen_variant.cu.
+using GenFn = cudaError_t (*)(int, const KParams*, int, int, size_t, cudaStream_t, int*);
+#define PSSO_DECL(v, m) \
+    cudaError_t gen_variant_##v##_##m(int, const KParams*, int, int, size_t, cudaStream_t, int*);
+PSSO_DECL(0, 1) PSSO_DECL(0, 2) PSSO_DECL(0, 4) PSSO_DECL(0, 8)
+PSSO_DECL(1, 1) PSSO_DECL(1, 2) PSSO_DECL(1, 4) PSSO_DECL(1, 8)
+PSSO_DECL(2, 1) PSSO_DECL(2, 2) PSSO_DECL(2, 4) PSSO_DECL(2, 8)
+#undef PSSO_DECL
 
 cudaError_t gen_call(int variant, int op, int mc_index, const KParams* p, int grid, int block,
                      size_t smem, cudaStream_t s, int* out)
 {
-    switch (variant) {
-    case 0: return gen_f64_lat64(op, mc_index, p, grid, block, smem, s, out);
-    case 1: return gen_f64_lat32(op, mc_index, p, grid, block, smem, s, out);
-    default: return gen_f32r(op, mc_index, p, grid, block, smem, s, out);
-    }
+    static const GenFn table[3][4] = {
+        {gen_variant_0_1, gen_variant_0_2, gen_variant_0_4, gen_variant_0_8},
+        {gen_variant_1_1, gen_variant_1_2, gen_variant_1_4, gen_variant_1_8},
+        {gen_variant_2_1, gen_variant_2_2, gen_variant_2_4, gen_variant_2_8}};
+    if (variant < 0 || variant > 2 || mc_index < 0 || mc_index > 3) return cudaErrorInvalidValue;
+    return table[variant][mc_index](op, p, grid, block, smem, s, out);
 }
 
 cudaError_t launch_best_f64(const InstDev* inst, int n_inst, int lattice, cudaStream_t s)

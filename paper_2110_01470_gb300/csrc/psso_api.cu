@@ -9,6 +9,8 @@
 
 #include "psso.h"
 #include "psso_internal.h"
+#include "rot_pipeline.h"
+#include "tc_gemm.cuh"
 
 using namespace psso;
 
@@ -62,6 +64,8 @@ struct HostInst {
     size_t off_X = 0, off_P = 0, off_pf64 = 0, off_plo = 0, off_phi = 0, off_pver = 0,
            off_pflag = 0, off_grow = 0, off_rec = 0, off_rec2 = 0, off_gb = 0, off_gbrow = 0,
            off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0, off_M64 = 0, off_M32 = 0;
+    bool tc = false;              // generations run by the tensor-core pipeline
+    rot::RotHost rh{};
 };
 
 }  // namespace
@@ -156,14 +160,27 @@ psso_status plan(psso_ctx* h)
     const int sbm = h->cfg.single_block_max == 0 ? 4 : (h->cfg.single_block_max < 0 ? 0 : h->cfg.single_block_max);
     size_t unit_smem_max = 0;
     double total_cost = 0.0;
-    for (auto& I : h->inst) {
+    int n_kernel = 0, only = -1;           // instances the persistent kernel runs
+    for (size_t k = 0; k < h->inst.size(); ++k) {
+        HostInst& I = h->inst[k];
         I.nchunks = (int)((I.pr.D + 3) / 4);
         I.Dp = 4 * I.nchunks;
         I.G = std::min(32, pow2_ceil(I.nchunks));
         I.maxc = pow2_ceil((I.nchunks + 31) / 32);
+        I.R = 1;
+        if (I.tc) continue;
+        ++n_kernel;
+        only = (int)k;
         unit_smem_max = std::max(unit_smem_max, align_up((size_t)I.Dp * h->pos_size, 16));
         total_cost += (double)I.pr.N * I.Dp;
         h->mc_index = std::max(h->mc_index, I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0);
+    }
+    if (n_kernel == 0) {                    // every instance runs on the tensor-core pipeline
+        h->grid = 0;
+        h->units.clear();
+        h->block_first.assign(1, 0);
+        h->smem = 0;
+        return PSSO_OK;
     }
     int max_threads = 0;
     CUDA_TRY(gen_call(h->variant, 3, h->mc_index, nullptr, 0, 0, 0, nullptr, &max_threads));
@@ -176,8 +193,8 @@ psso_status plan(psso_ctx* h)
     // One multi-block swarm: a control warp plus enough compute warps for one
     // particle per compute group and about one block per SM (pipelined blocks).
     bool pipe = false;
-    if (h->inst.size() == 1 && h->cfg.pipeline != 2) {
-        const HostInst& I = h->inst[0];
+    if (n_kernel == 1 && h->cfg.pipeline != 2) {
+        const HostInst& I = h->inst[only];
         const int gpw = 32 / I.G;
         const int64_t groups = (I.pr.N + gpw - 1) / gpw;
         const int64_t single_passes = (I.pr.N + (int64_t)nw * gpw - 1) / ((int64_t)nw * gpw);
@@ -208,6 +225,10 @@ psso_status plan(psso_ctx* h)
         int64_t sumR = 0;
         for (size_t k = 0; k < h->inst.size(); ++k) {
             const HostInst& I = h->inst[k];
+            if (I.tc) {
+                R[k] = 1;               // no blocks of the persistent kernel
+                continue;
+            }
             const int ppp = (pipe ? nw - 1 : nw) * (32 / I.G);
             const int64_t passes = (I.pr.N + ppp - 1) / ppp;
             int64_t r = 1;
@@ -237,6 +258,7 @@ psso_status plan(psso_ctx* h)
         for (size_t k = 0; k < h->inst.size(); ++k) {
             HostInst& I = h->inst[k];
             I.R = R[k];
+            if (I.tc) continue;
             const int ppp = (pipe ? nw - 1 : nw) * (32 / I.G);
             const int64_t passes = (I.pr.N + ppp - 1) / ppp;
             for (int r = 0; r < R[k]; ++r) {
@@ -389,7 +411,71 @@ psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
     p.g_end = g_end;
     p.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : (int64_t)50000000;
     p.fault_skip_rank = h->cfg.fault_skip_rank;
-    CUDA_TRY(launch_variant(h->variant, h->mc_index, p, h->grid, h->block, h->smem, h->stream));
+    if (h->grid > 0)
+        CUDA_TRY(launch_variant(h->variant, h->mc_index, p, h->grid, h->block, h->smem, h->stream));
+    for (auto& I : h->inst) {
+        if (!I.tc) continue;
+        CUDA_TRY(rot::set_generation(I.rh, g_begin, h->stream));
+        for (int64_t g = g_begin; g <= g_end; ++g) CUDA_TRY(rot::enqueue_generation(I.rh, h->stream));
+    }
+    return PSSO_OK;
+}
+
+// Buffers, tensor maps and constant operand planes of a tensor-pipeline instance.
+psso_status setup_tc(psso_ctx* h, size_t k)
+{
+    HostInst& I = h->inst[k];
+    rot::RotHost& R = I.rh;
+    rot::RotDev& r = R.dev;
+    const int64_t N = I.pr.N;
+    const int D = (int)I.pr.D;
+    r.fn = I.pr.fn;
+    r.D = D;
+    r.N = N;
+    r.Np = (int)((N + tc::BM - 1) / tc::BM * tc::BM);
+    r.Jp = (D + tc::BN - 1) / tc::BN * tc::BN;
+    r.Kp = (D + tc::BK - 1) / tc::BK * tc::BK;
+    r.nJt = r.Jp / tc::BN;
+    r.zc = tc::z_err_per_s(r.Kp);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = align_up(off, 256);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
+    const size_t oA = take((size_t)3 * r.Np * r.Kp * 2), oB = take((size_t)3 * r.Jp * r.Kp * 2),
+                 omn = take((size_t)r.Jp * 4), odn = take((size_t)r.Np * 4), osame = take((size_t)N * 4),
+                 opart = take((size_t)N * r.nJt * 16), ol1 = take((size_t)N * 4), ol2 = take((size_t)N * 4),
+                 oz = take((size_t)2 * N * I.Dp * 8), oz0 = take((size_t)I.Dp * 8),
+                 octl = take(sizeof(rot::RotCtl));
+    R.mem_bytes = align_up(off, 256);
+    CUDA_TRY(cudaMalloc(&R.mem, R.mem_bytes));
+    CUDA_TRY(cudaMemsetAsync(R.mem, 0, R.mem_bytes, h->stream));
+    char* b = static_cast<char*>(R.mem);
+    r.A = reinterpret_cast<__nv_bfloat16*>(b + oA);
+    R.B = reinterpret_cast<__nv_bfloat16*>(b + oB);
+    r.mnorm = reinterpret_cast<float*>(b + omn);
+    r.dnorm = reinterpret_cast<float*>(b + odn);
+    r.same = reinterpret_cast<uint32_t*>(b + osame);
+    r.part = reinterpret_cast<float4*>(b + opart);
+    r.list1 = reinterpret_cast<int32_t*>(b + ol1);
+    r.list2 = reinterpret_cast<int32_t*>(b + ol2);
+    r.zbuf = reinterpret_cast<double*>(b + oz);
+    r.zero64 = reinterpret_cast<const double*>(b + oz0);
+    r.ctl = reinterpret_cast<rot::RotCtl*>(b + octl);
+    r.inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev) + k;
+    r.inst_w32 = I.w.empty() ? nullptr : reinterpret_cast<const float*>(h->arena + I.off_w32);
+    R.M32 = reinterpret_cast<const float*>(h->arena + I.off_M32);
+    R.N = N;
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
+    R.z64_grid = 2 * prop.multiProcessorCount;
+    R.fix_grid = prop.multiProcessorCount;
+    if (!tc::make_tmap_bf16(&R.tmA, r.A, r.Kp, 3 * r.Np) || !tc::make_tmap_bf16(&R.tmB, R.B, r.Kp, 3 * r.Jp))
+        return fail(PSSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core operands");
+    CUDA_TRY(rot::configure());
+    CUDA_TRY(rot::build_constants(R, h->stream));
     return PSSO_OK;
 }
 
@@ -399,6 +485,15 @@ psso_status read_status(psso_ctx* h)
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     StatusDev st;
     CUDA_TRY(cudaMemcpy(&st, h->arena + h->off_status, sizeof st, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < h->inst.size(); ++k) {
+        if (!h->inst[k].tc) continue;
+        int tst = 0;
+        CUDA_TRY(cudaMemcpy(&tst, &h->inst[k].rh.dev.ctl->status, sizeof tst, cudaMemcpyDeviceToHost));
+        if (tst) {
+            h->failed = true;
+            return fail(PSSO_ERR_TIMEOUT, "a tensor-core pipeline wait ran out (instance " + std::to_string(k) + ")");
+        }
+    }
     if (st.err != 0) {
         h->failed = true;
         return fail((psso_status)st.err, "a cross-block wait ran out (instance " +
@@ -433,6 +528,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     if (c.fault_skip_rank < 0) return fail(PSSO_ERR_ARG, "fault_skip_rank must be >= 0");
     if (c.residency != 0 && c.residency != 2) return fail(PSSO_ERR_ARG, "residency must be 0 or 2");
     if (c.pipeline != 0 && c.pipeline != 2) return fail(PSSO_ERR_ARG, "pipeline must be 0 or 2");
+    if (c.tensor_rotation < -1 || c.tensor_rotation > 1) return fail(PSSO_ERR_ARG, "tensor_rotation must be -1, 0 or 1");
     for (int32_t k = 0; k < count; ++k) {
         psso_status st = check_problem(problems[k], c.precision, k);
         if (st != PSSO_OK) return st;
@@ -462,6 +558,8 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         if (I.pr.weights) I.w.assign(I.pr.weights, I.pr.weights + I.pr.D);
         if (I.pr.fn >= PSSO_ROT_ELLIPSOID) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
+        I.tc = h->precision == PSSO_PREC_F32_RECHECK && I.pr.fn >= PSSO_ROT_ELLIPSOID &&
+               (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32));
     }
     psso_status st = plan(h);
     if (st != PSSO_OK) {
@@ -576,6 +674,11 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         fail(PSSO_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
         return cleanup_fail(PSSO_ERR_CUDA);
     }
+    for (size_t k = 0; k < h->inst.size(); ++k) {
+        if (!h->inst[k].tc) continue;
+        st = setup_tc(h, k);
+        if (st != PSSO_OK) return cleanup_fail(st);
+    }
     st = launch(h, 0, 0);
     if (st != PSSO_OK) return cleanup_fail(st);
     for (auto& I : h->inst) h->evals += I.pr.N;
@@ -637,6 +740,8 @@ psso_status psso_reset(psso_handle h)
         CUDA_TRY(cudaMemsetAsync(h->arena + I.off_gb, 0, sizeof(GBestDev), h->stream));
     }
     CUDA_TRY(cudaMemsetAsync(h->arena + h->off_status, 0, sizeof(StatusDev), h->stream));
+    for (auto& I : h->inst)
+        if (I.tc) CUDA_TRY(cudaMemsetAsync(&I.rh.dev.ctl->status, 0, sizeof(int), h->stream));
     psso_status st = launch(h, 0, 0);
     if (st != PSSO_OK) return st;
     h->gen = 0;
@@ -833,6 +938,8 @@ psso_status psso_load(psso_handle h, const void* buf, size_t n)
     CUDA_TRY(cudaMemcpy(h->arena + h->state_off, static_cast<const char*>(buf) + sizeof hd, state,
                         cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(h->arena + h->off_status, 0, sizeof(StatusDev)));
+    for (auto& I : h->inst)
+        if (I.tc) CUDA_TRY(cudaMemset(&I.rh.dev.ctl->status, 0, sizeof(int)));
     h->gen = hd.gen;
     h->evals = hd.evals;
     h->updates = hd.updates;
@@ -848,6 +955,8 @@ void psso_destroy(psso_handle h)
         cudaStreamSynchronize(h->stream);
         cudaFree(h->arena);
     }
+    for (auto& I : h->inst)
+        if (I.rh.mem) cudaFree(I.rh.mem);
     delete h;
 }
 

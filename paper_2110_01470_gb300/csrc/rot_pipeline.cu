@@ -1,0 +1,528 @@
+// rot_pipeline.cu -- one SSO generation of a rotated-function swarm with
+// FP32 fitness and FP64 recheck, as a short sequence of kernels around the
+// tensor-core rotation (z = M (x - o) for the whole swarm is one N x D x D
+// GEMM, which the per-particle persistent kernel cannot share across
+// particles).
+//
+// Generation g (the number g is read from device memory, so the sequence can
+// be replayed by a CUDA graph):
+//   1. rot_update    Eq. 2.1 for every variable (the same draws as the
+//                    persistent kernel), X written in place, d = fl32(x - o)
+//                    split into the three BF16 planes, ||d|| bound per row,
+//                    "x equals pBest" flag per row.
+//   2. rot_gemm_fit  the tcgen05 GEMM; its epilogue turns each z into the
+//                    function's FP32 terms and per-term error bounds and
+//                    writes per-(particle, 128-column tile) partial sums.
+//   3. rot_decide    FP32 fitness and bound per particle; pBest update when
+//                    the interval decides it (Alg. 3, <=); else the particle
+//                    goes on the recheck list.
+//   4. rot_z64       FP64 z = M (x - o) of listed rows in the oracle's order
+//                    (k ascending, fma from +0), one thread per output.
+//   5. rot_fix       FP64 fitness of those rows (the oracle's summation) and
+//                    the exact pBest decision.
+//   6. rot_argmin(0) gBest candidates (Alg. 4, lowest index): unique from the
+//                    intervals, or the pBests that can still be the minimum
+//                    go on a second list.
+//   7-8.             steps 4-5 for that list (pBest rows only).
+//   9. rot_argmin(1) the exact arg-min if needed, gBest record, log, gBest
+//                    row, generation counter + 1.
+// Steps 4-5 and 7-8 exit at once when their list is empty.
+#include <cfloat>
+#include <climits>
+#include <cuda_bf16.h>
+
+#include "psso.h"
+#include "psso_internal.h"
+#include "rot_pipeline.h"
+#include "sso_kernel.cuh"
+#include "tc_gemm.cuh"
+
+namespace psso {
+namespace rot {
+
+using tc::BM;
+using tc::BN;
+
+__global__ void set_gen(RotCtl* ctl, long long g)
+{
+    ctl->gen = g;
+    ctl->n1 = 0;
+    ctl->n2 = 0;
+    ctl->amb = 0;
+    ctl->acc = 0;
+    ctl->rck = 0;
+}
+
+// ---- 1. update --------------------------------------------------------------
+template <int MAXC>
+__device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
+{
+    const int lane = threadIdx.x & 31;
+    const InstDev& d = *r.inst;
+    float* xr = static_cast<float*>(d.X) + i * in.Dp;
+    const float* pr = static_cast<const float*>(d.P) + i * in.Dp;
+    const float* gs = static_cast<const float*>(d.gbrow);
+    const uint32_t gg = (uint32_t)g;
+    const uint32_t ctr3r = TAG_RHO | (in.sid << 8), ctr3f = TAG_FRESH | (in.sid << 8);
+    bool eqp = true;
+    float ss = 0.f;
+    const size_t plane = (size_t)r.Np * r.Kp;
+    __nv_bfloat16* arow = r.A + (size_t)i * r.Kp;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane + 32 * q;
+        if (c >= in.nchunks) continue;
+        const int nvalid = min(4, in.D - 4 * c);
+        const uint32_t valid = (1u << nvalid) - 1u;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (g == 0) {
+            fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+        } else {
+            const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+            const uint4 fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+            float xo[4], po[4], go[4];
+            ld4(xr + 4 * c, xo);
+            ld4(pr + 4 * c, po);
+            ld4(gs + 4 * c, go);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t w = word_of(rb, m);
+                const bool lg = (w < in.Tg32) || (in.tfull & 1u);
+                const bool lp = (w < in.Tp32) || (in.tfull & 2u);
+                const bool lw = (w < in.Tw32) || (in.tfull & 4u);
+                x[m] = lg ? go[m] : lp ? po[m] : lw ? xo[m] : fresh_f32(word_of(fb, m), in);
+                if (m >= nvalid) x[m] = 0.f;
+                eqp = eqp && same_bits(x[m], po[m]);
+            }
+        }
+        st4(xr + 4 * c, x);
+        __nv_bfloat16 h[4], mm[4], l[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * c + m;
+            const float dv = (j < in.D) ? __fsub_rn(x[m], __ldg(in.o32 + j)) : 0.f;
+            ss = __fmaf_rn(dv, dv, ss);
+            tc::split3(dv, h[m], mm[m], l[m]);
+        }
+        // 4 consecutive bf16 (8 bytes) per plane
+        auto pack = [](const __nv_bfloat16 (&v)[4]) {
+            uint2 u;
+            u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+            u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+            return u;
+        };
+        *reinterpret_cast<uint2*>(arow + 4 * c) = pack(h);
+        *reinterpret_cast<uint2*>(arow + plane + 4 * c) = pack(mm);
+        *reinterpret_cast<uint2*>(arow + 2 * plane + 4 * c) = pack(l);
+    }
+    for (int off = 16; off > 0; off >>= 1) ss = __fadd_rn(ss, __shfl_xor_sync(0xffffffffu, ss, off));
+    eqp = __all_sync(0xffffffffu, eqp);
+    if (lane == 0) {
+        // sum of 4 MAXC products per lane and 5 butterfly levels: relative error
+        // below (4 MAXC + 6) u; the bound is rounded up
+        const float rel = 1.02f * (float)(4 * MAXC + 6) * 0x1p-24f;
+        r.dnorm[i] = __fsqrt_ru(__fmul_ru(ss, 1.f + rel));
+        r.same[i] = (g > 0 && eqp) ? 1u : 0u;
+    }
+}
+
+__global__ void rot_update(const RotDev r)
+{
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const InstDev& d = *r.inst;
+    if (i >= d.N) return;
+    const Hot in = hot_of(d);
+    const int64_t g = r.ctl->gen;
+    switch (in.maxc) {
+    case 1: update_row<1>(r, in, i, g); break;
+    case 2: update_row<2>(r, in, i, g); break;
+    case 4: update_row<4>(r, in, i, g); break;
+    default: update_row<8>(r, in, i, g); break;
+    }
+}
+
+// ---- 2. GEMM with the fitness epilogue ------------------------------------------
+// Per element z~ with error ez <= zc ||d|| ||M_j|| + u |z~| (see tc_gemm.cuh),
+// the terms and bounds of the rotated functions (as in the FP32 path of the
+// persistent kernel): ellipsoid w z^2; Rastrigin z^2 + 20 sin^2(pi z);
+// Ackley z^2 and sin^2(pi z) (two sums).  Sums: 32 terms per column block,
+// then 4 blocks per tile, then the tiles (in rot_decide).
+struct FitEpi {
+    const RotDev* r;
+    int fn, D;
+    float dn, acc, acc2, accE, rQ;
+    __device__ void operator()(int c, const float (&z)[32])
+    {
+        const int j0 = blockIdx.y * BN + 32 * c;
+        float s = 0.f, s2 = 0.f, e = 0.f, eq = 0.f;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int j = j0 + t;
+            if (j >= D) break;
+            const float zt = z[t];
+            const float az = fabsf(zt);
+            const float ez = 1.01f * __fmaf_rn(r->zc * dn, __ldg(r->mnorm + j), 0x1p-24f * az);
+            const float xi = az + ez;
+            if (fn == FN_ELLIPSOID) {
+                const float w = __ldg(r->inst_w32 + j);
+                const float tv = __fmul_rn(w, __fmul_rn(zt, zt));
+                s = __fadd_rn(s, tv);
+                e = __fadd_rn(e, 4.2f * 0x1p-24f * tv + 1.01f * w * (2.f * az + ez) * ez);
+            } else if (fn == FN_RASTRIGIN) {
+                const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
+                const float tv = __fmaf_rn(zt, zt, __fmul_rn(20.f, __fmul_rn(sn, sn)));
+                s = __fadd_rn(s, tv);
+                e = __fadd_rn(e, (2.f * SINPI32_ERR_U + 4.f) * 0x1p-24f * tv +
+                                     1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ez);
+            } else {   // Ackley
+                s = __fadd_rn(s, __fmul_rn(zt, zt));
+                const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
+                s2 = __fadd_rn(s2, __fmul_rn(sn, sn));
+                e = __fadd_rn(e, 1.01f * (2.f * az + ez) * ez);
+                eq = __fadd_rn(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ez);
+            }
+        }
+        acc = __fadd_rn(acc, s);
+        acc2 = __fadd_rn(acc2, s2);
+        accE = __fadd_rn(accE, e);
+        rQ = __fadd_rn(rQ, eq);
+        if (c == BN / 32 - 1) {
+            const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
+            if (i < r->N) r->part[i * r->nJt + blockIdx.y] = make_float4(acc, acc2, accE, rQ);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(128, 1)
+    rot_gemm_fit(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ RotDev r)
+{
+    const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
+    FitEpi epi{&r, base_fn(r.fn), r.D, i < r.N ? r.dnorm[i] : 0.f, 0.f, 0.f, 0.f, 0.f};
+    tc::GemmArgs a{r.Np, r.Jp, r.Kp, &r.ctl->status};
+    tc::gemm_tile(&tmA, &tmB, a, epi);
+}
+
+// ---- 3. FP32 decisions ------------------------------------------------------------
+// FP32 fitness and its bound from the tile sums (the rotated branches of the
+// FP32 path; csum = summation depth 32 + 4 + tiles, + 2).
+__device__ inline Fit32 rot_final(int fn, int D, float acc, float acc2, float accE, float rQ, int ntiles)
+{
+    const float U = 0x1p-24f;
+    const float csum = 38.f + (float)ntiles;
+    Fit32 f;
+    if (fn != FN_ACKLEY) {
+        f.f = acc;
+        f.E = 1.1f * (accE + csum * U * acc);
+        f.E = __fadd_ru(f.E, 0x1p-40f * (acc + accE));
+        return f;
+    }
+    const float Df = (float)D;
+    const float A = __fsqrt_rn(__fdiv_rn(acc, Df));
+    const float B = expm1_f32(__fmul_rn(-0.2f, A));
+    const float C = expm1_f32(__fmul_rn(-2.f, __fdiv_rn(acc2, Df)));
+    const float f1 = __fmul_rn(-20.f, B), f2 = __fmul_rn(-0x1.5bf0a8p+1f, C);
+    f.f = __fadd_rn(f1, f2);
+    const float ES = accE + (3.1f + csum) * U * acc;
+    const float EQ = rQ + (2.f * SINPI32_ERR_U + 1.f + csum) * U * acc2;
+    const float d1 = (ES <= 0.5f * acc) ? 1.5f * f1 * ES / acc : 4.f * __fsqrt_ru(ES / Df);
+    f.E = 1.1f * (d1 + (EXPM1F_ERR_U + 6.f) * U * f1 + (2.f * 2.7182818f / Df) * EQ +
+                  (EXPM1F_ERR_U + 8.f) * U * f2 + U * f.f);
+    f.E = __fadd_ru(f.E, 0x1p-40f * (f.f + accE));
+    return f;
+}
+
+__global__ void rot_decide(const RotDev r)
+{
+    __shared__ unsigned long long blk_acc;
+    if (threadIdx.x == 0) blk_acc = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const InstDev& d = *r.inst;
+    const int64_t g = r.ctl->gen;
+    if (i < d.N) {
+        // tile sums in tile order by lane 0 (a fixed order)
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < r.nJt) p = r.part[i * r.nJt + lane];
+        float a = 0.f, a2 = 0.f, ae = 0.f, aq = 0.f;
+        for (int t = 0; t < r.nJt; ++t) {
+            a = __fadd_rn(a, __shfl_sync(0xffffffffu, p.x, t));
+            a2 = __fadd_rn(a2, __shfl_sync(0xffffffffu, p.y, t));
+            ae = __fadd_rn(ae, __shfl_sync(0xffffffffu, p.z, t));
+            aq = __fadd_rn(aq, __shfl_sync(0xffffffffu, p.w, t));
+        }
+        const Fit32 f = rot_final(base_fn(r.fn), r.D, a, a2, ae, aq, r.nJt);
+        const float lo = __fsub_rd(f.f, f.E), hi = __fadd_ru(f.f, f.E);
+        int accept = 0, write = 0, undecided = 0;
+        if (g == 0) {
+            accept = write = 1;
+        } else if (r.same[i]) {
+            accept = 1;              // identical row: identical fitness, state unchanged
+        } else if (hi < d.plo[i]) {
+            accept = write = 1;
+        } else if (!(lo > d.phi[i])) {
+            undecided = 1;
+        }
+        if (write) {
+            const float* xr = static_cast<const float*>(d.X) + i * d.Dp;
+            float* prow = static_cast<float*>(d.P) + i * d.Dp;
+            for (int c = lane; c < d.nchunks; c += 32) {
+                float v[4];
+                ld4(xr + 4 * c, v);
+                st4(prow + 4 * c, v);
+            }
+            if (lane == 0) {
+                d.plo[i] = lo;
+                d.phi[i] = hi;
+                d.pflag[i] = 0u;
+                d.pf64[i] = 0.0;
+                d.pver[i] = (uint32_t)g;
+            }
+        }
+        if (lane == 0) {
+            if (undecided) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i;
+            if (accept) atomicAdd(&blk_acc, 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_acc) atomicAdd(&r.ctl->acc, blk_acc);
+}
+
+// ---- 4/7. FP64 rotation of listed rows ------------------------------------------------
+// which = 1: entries of list1, row 2e = X_i and row 2e+1 = P_i when its FP64
+// value is not known; which = 2: entries of list2, row 2e+1 = P_i.
+__global__ void rot_z64(const RotDev r, int which)
+{
+    __shared__ double dsh[1024];
+    const InstDev& d = *r.inst;
+    const unsigned n = which == 1 ? r.ctl->n1 : r.ctl->n2;
+    const int D = r.D;
+    const int nJb = (D + 127) / 128;
+    const long long items = (long long)n * 2 * nJb;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int jb = (int)(it % nJb);
+        const int row = (int)((it / nJb) & 1);
+        const long long e = it / nJb / 2;
+        const int32_t i = which == 1 ? r.list1[e] : r.list2[e];
+        const bool needed = which == 1 ? (row == 0 || !(d.pflag[i] & 1u)) : row == 1;
+        if (!needed) continue;          // uniform over the block
+        const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
+        __syncthreads();
+        for (int k = threadIdx.x; k < D; k += blockDim.x) dsh[k] = __dsub_rn((double)src[k], d.o64[k]);
+        __syncthreads();
+        const int j = jb * 128 + threadIdx.x;
+        double* out = r.zbuf + (size_t)(2 * e + row) * d.Dp;
+        if (j < D) {
+            const double* mrow = d.M64 + (size_t)j * D;
+            double z = 0.0;
+            for (int k = 0; k < D; ++k) z = __fma_rn(__ldg(mrow + k), dsh[k], z);
+            out[j] = z;
+        } else if (j < d.Dp) {
+            out[j] = 0.0;
+        }
+    }
+}
+
+// ---- 5/8. FP64 fitness of the rotated rows and the exact decisions --------------------
+__device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long e, int lane)
+{
+    Hot hz = hot_of(d);
+    hz.fn = base_fn(d.fn);   // the rows hold z already: the unrotated function with o = 0
+    hz.o64 = r.zero64;
+    const int64_t g = r.ctl->gen;
+    const double* zx = r.zbuf + (size_t)(2 * e) * d.Dp;
+    const double* zp = zx + d.Dp;
+    if (which == 1) {
+        const int32_t i = r.list1[e];
+        const bool have_p = (d.pflag[i] & 1u) != 0;
+        const double fx = fit64_row<double>(hz, zx, false);
+        const double fp = have_p ? d.pf64[i] : fit64_row<double>(hz, zp, false);
+        const bool accept = fx <= fp;
+        if (accept) {
+            const float* xr = static_cast<const float*>(d.X) + (int64_t)i * d.Dp;
+            float* prow = static_cast<float*>(d.P) + (int64_t)i * d.Dp;
+            for (int c = lane; c < d.nchunks; c += 32) {
+                float v[4];
+                ld4(xr + 4 * c, v);
+                st4(prow + 4 * c, v);
+            }
+        }
+        if (lane == 0) {
+            const double v = accept ? fx : fp;
+            d.pf64[i] = v;
+            d.pflag[i] = 1u;
+            d.plo[i] = f64_to_f32_rd(v);
+            d.phi[i] = f64_to_f32_ru(v);
+            if (accept) d.pver[i] = (uint32_t)g;
+            atomicAdd(&r.ctl->rck, have_p ? 1ull : 2ull);
+            if (accept) atomicAdd(&r.ctl->acc, 1ull);
+        }
+    } else {
+        const int32_t i = r.list2[e];
+        const double fp = fit64_row<double>(hz, zp, false);
+        if (lane == 0) {
+            d.pf64[i] = fp;
+            d.pflag[i] = 1u;
+            d.plo[i] = f64_to_f32_rd(fp);
+            d.phi[i] = f64_to_f32_ru(fp);
+            atomicAdd(&r.ctl->rck, 1ull);
+        }
+    }
+}
+
+__global__ void rot_fix(const RotDev r, int which)
+{
+    const int lane = threadIdx.x & 31;
+    const InstDev& d = *r.inst;
+    const unsigned n = which == 1 ? r.ctl->n1 : r.ctl->n2;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < (long long)n;
+         e += nwarps)
+        fix_one(r, d, which, e, lane);
+}
+
+
+// ---- 6/9. gBest --------------------------------------------------------------------------
+template <bool F32R>
+__device__ Cand block_reduce_cand(Cand c, Cand* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
+    if (lane == 0) sh[w] = c;
+    __syncthreads();
+    if (w == 0) {
+        c = lane < nw ? sh[lane] : cand_none();
+        for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
+        if (lane == 0) sh[0] = c;
+    }
+    __syncthreads();
+    const Cand out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
+{
+    __shared__ Cand sh[32];
+    __shared__ unsigned n2;
+    const InstDev& d = *r.inst;
+    RotCtl* ctl = r.ctl;
+    const int64_t g = ctl->gen;
+    const int64_t N = d.N;
+    if (phase == 0) {
+        Cand c = cand_none();
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+            c = cand_merge<true>(c, cand_of<true>((long long)i, d.pf64[i], d.plo[i], d.phi[i],
+                                                  (int)(d.pflag[i] & 1u), d.pver[i]));
+        const Cand b = block_reduce_cand<true>(c, sh);
+        if (b.l2 > b.mh) {          // one interval lies below every other: the arg-min
+            if (threadIdx.x == 0) {
+                ctl->amb = 0;
+                ctl->win_i = b.i;
+                ctl->win_v = b.v;
+                ctl->win_lo = b.l1;
+                ctl->win_hi = b.h1;
+                ctl->win_has = b.has1;
+                ctl->win_ver = b.ver;
+            }
+            return;
+        }
+        // several pBests may be the minimum: those without an FP64 value go on list2
+        if (threadIdx.x == 0) n2 = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+            if (d.plo[i] <= b.mh && !(d.pflag[i] & 1u)) r.list2[atomicAdd(&n2, 1u)] = (int32_t)i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ctl->amb = 1;
+            ctl->n2 = n2;
+        }
+        return;
+    }
+    // phase 1
+    if (ctl->amb) {
+        // every pBest that can be the minimum now has its FP64 value; the others
+        // have a lower bound above the smallest upper bound
+        Cand c = cand_none();
+        for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+            if (d.pflag[i] & 1u) {
+                Cand q = cand_none();
+                q.v = d.pf64[i];
+                q.i = (long long)i;
+                q.ver = d.pver[i];
+                c = cand_merge<false>(c, q);
+            }
+        const Cand b = block_reduce_cand<false>(c, sh);
+        if (threadIdx.x == 0) {
+            ctl->win_i = b.i;
+            ctl->win_v = b.v;
+            ctl->win_lo = f64_to_f32_rd(b.v);
+            ctl->win_hi = f64_to_f32_ru(b.v);
+            ctl->win_has = 1;
+            ctl->win_ver = b.ver;
+        }
+        __syncthreads();
+    }
+    const long long wi = ctl->win_i;
+    const float* src = static_cast<const float*>(d.P) + wi * d.Dp;
+    float* dst = static_cast<float*>(d.gbrow);
+    for (int j = threadIdx.x; j < d.Dp; j += blockDim.x) dst[j] = src[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Winner w;
+        w.idx = wi;
+        w.has64 = ctl->win_has;
+        w.f64 = w.has64 ? ctl->win_v : 0.0;
+        w.lo = ctl->win_lo;
+        w.hi = ctl->win_hi;
+        w.ver = ctl->win_ver;
+        w.acc = ctl->acc;
+        w.rck = ctl->rck;
+        write_gbest(d, w, g);
+        ctl->gen = g + 1;
+        ctl->n1 = 0;
+        ctl->n2 = 0;
+        ctl->amb = 0;
+        ctl->acc = 0;
+        ctl->rck = 0;
+    }
+}
+
+// ---- host --------------------------------------------------------------------------------
+cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s)
+{
+    const RotDev& r = h.dev;
+    const int N = (int)h.N;
+    const int wpb = 8;
+    rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
+    rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / BN), 128, tc::SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
+    rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
+    rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 1);
+    rot_fix<<<h.fix_grid, 32 * wpb, 0, s>>>(r, 1);
+    rot_argmin<<<1, 1024, 0, s>>>(r, 0);
+    rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 2);
+    rot_fix<<<h.fix_grid, 32 * wpb, 0, s>>>(r, 2);
+    rot_argmin<<<1, 1024, 0, s>>>(r, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t build_constants(const RotHost& h, cudaStream_t s)
+{
+    const RotDev& r = h.dev;
+    return tc::launch_split_matrix(h.M32, r.D, r.Jp, r.Kp, h.B, r.mnorm, s);
+}
+
+cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s)
+{
+    set_gen<<<1, 1, 0, s>>>(h.dev.ctl, g);
+    return cudaGetLastError();
+}
+
+cudaError_t configure()
+{
+    return cudaFuncSetAttribute(rot_gemm_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+}
+
+}  // namespace rot
+}  // namespace psso

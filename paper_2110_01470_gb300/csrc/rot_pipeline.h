@@ -1,0 +1,68 @@
+// rot_pipeline.h -- descriptors of the tensor-core generation pipeline for
+// rotated-function swarms with FP32 fitness and FP64 recheck.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "psso_internal.h"
+
+namespace psso {
+namespace rot {
+
+// Per-instance control block in device memory.
+struct RotCtl {
+    long long gen;                 // generation the next kernels run
+    unsigned n1, n2;               // recheck list lengths (decisions, arg-min)
+    int amb;                       // the arg-min needs the exact pass
+    int status;                    // a tensor-core pipeline wait ran out
+    unsigned long long acc, rck;   // pBest updates / FP64 evaluations this generation
+    long long win_i;               // gBest of this generation
+    double win_v;
+    float win_lo, win_hi;
+    uint32_t win_ver;
+    int win_has;
+};
+
+struct RotDev {
+    const InstDev* inst;
+    const float* inst_w32;
+    int fn, D;
+    long long N;
+    int Np, Jp, Kp, nJt;           // padded extents, 128-column tiles
+    float zc;                      // z error per unit of ||d|| ||M_j||
+    __nv_bfloat16* A;              // [3][Np][Kp] split planes of d = x - o
+    float* mnorm;                  // [Jp] bound on ||M32_j||
+    float* dnorm;                  // [Np] bound on ||d_i||
+    uint32_t* same;                // [N] x_i equals pBest_i bit for bit
+    float4* part;                  // [N][nJt] tile sums (s1, s2, e1, e2)
+    int32_t* list1;                // [N] undecided pBest updates
+    int32_t* list2;                // [N] pBests that may be the minimum
+    double* zbuf;                  // [2N][Dp] FP64 z rows of listed particles
+    const double* zero64;          // [Dp] zeros
+    RotCtl* ctl;
+};
+
+struct RotHost {
+    RotDev dev;
+    CUtensorMap tmA, tmB;
+    __nv_bfloat16* B;              // [3][Jp][Kp] split planes of M32
+    const float* M32;
+    long long N;
+    int z64_grid, fix_grid;
+    void* mem;                     // the one allocation holding the buffers above
+    size_t mem_bytes;
+};
+
+cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s);
+cudaError_t build_constants(const RotHost& h, cudaStream_t s);
+cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s);
+cudaError_t configure();
+
+}  // namespace rot
+
+namespace tc {
+cudaError_t launch_split_matrix(const float* M32, int D, int Jp, int Kp, __nv_bfloat16* B, float* mnorm,
+                                cudaStream_t s);
+}  // namespace tc
+}  // namespace psso

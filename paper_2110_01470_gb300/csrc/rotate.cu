@@ -9,6 +9,7 @@
 #include "psso.h"
 #include "psso_internal.h"
 #include "sso_common.cuh"
+#include "rot_pipeline.h"
 #include "tc_gemm.cuh"
 
 namespace psso {
@@ -82,6 +83,13 @@ __global__ void split_rows(const float* __restrict__ X, const float* __restrict_
         A[plane + p] = m;
         A[2 * plane + p] = l;
     }
+}
+
+cudaError_t launch_split_matrix(const float* M32, int D, int Jp, int Kp, __nv_bfloat16* B, float* mnorm,
+                                cudaStream_t s)
+{
+    split_matrix<<<Jp, 256, 0, s>>>(M32, D, Jp, Kp, B, mnorm);
+    return cudaGetLastError();
 }
 
 struct ZEpi {

@@ -184,10 +184,17 @@ __device__ __forceinline__ int base_fn(int fn)
 // z = M d, d = x - o, for the group's own variables (lane_g owns chunks
 // lane_g + 32 q): z_j = sum_k M_jk d_k with k ascending from +0.0 by fma, each
 // d_k broadcast from the lane that holds it -- the oracle's order.
+template <class T, int MAXC>
+struct RowBuf {
+    T v[MAXC][4];
+};
+
 template <class Pos, int MAXC>
-__device__ __forceinline__ void rot_matvec64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g,
-                                             unsigned gmask, int G, double (&z)[MAXC][4])
+__device__ __noinline__ void rot_matvec64_impl(const Hot& in, const RowBuf<Pos, MAXC>& xb, int lane_g,
+                                               unsigned gmask, int G, RowBuf<double, MAXC>& zb)
 {
+    const auto& x = xb.v;
+    auto& z = zb.v;
     const int D = in.D;
     double d[MAXC][4];
 #pragma unroll
@@ -218,6 +225,26 @@ __device__ __forceinline__ void rot_matvec64(const Hot& in, const Pos (&x)[MAXC]
             }
         }
     }
+}
+
+// The matvecs are out of line (one copy per width instead of one per call
+// site); the rows go through small buffers so that the callers' arrays stay
+// in registers.
+template <class Pos, int MAXC>
+__device__ __forceinline__ void rot_matvec64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g,
+                                             unsigned gmask, int G, double (&z)[MAXC][4])
+{
+    RowBuf<Pos, MAXC> xb;
+    RowBuf<double, MAXC> zb;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+    rot_matvec64_impl<Pos, MAXC>(in, xb, lane_g, gmask, G, zb);
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) z[q][m] = zb.v[q][m];
 }
 
 template <class Pos, int MAXC>
@@ -324,10 +351,13 @@ struct Fit32 {
 // |z~ - z| <= (gamma_32 + gamma_nb + 2u) S (1 + O(u)), nb = number of blocks --
 // the fma chains, the block sums, M's rounding and d's rounding.
 template <int MAXC>
-__device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAXC][4], int lane_g,
-                                             unsigned gmask, int G, float (&z)[MAXC][4],
-                                             float (&ez)[MAXC][4])
+__device__ __noinline__ void rot_matvec32_impl(const Hot& in, const RowBuf<float, MAXC>& xb, int lane_g,
+                                               unsigned gmask, int G, RowBuf<float, MAXC>& zb,
+                                               RowBuf<float, MAXC>& eb)
 {
+    const auto& x = xb.v;
+    auto& z = zb.v;
+    auto& ez = eb.v;
     const int D = in.D;
     float d[MAXC][4], t[MAXC][4];
 #pragma unroll
@@ -384,6 +414,26 @@ __device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAX
     for (int q = 0; q < MAXC; ++q)
 #pragma unroll
         for (int m = 0; m < 4; ++m) ez[q][m] = c * ez[q][m] * (1.f + (float)D * U32);
+}
+
+template <int MAXC>
+__device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAXC][4], int lane_g,
+                                             unsigned gmask, int G, float (&z)[MAXC][4],
+                                             float (&ez)[MAXC][4])
+{
+    RowBuf<float, MAXC> xb, zb, eb;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+    rot_matvec32_impl<MAXC>(in, xb, lane_g, gmask, G, zb, eb);
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            z[q][m] = zb.v[q][m];
+            ez[q][m] = eb.v[q][m];
+        }
 }
 
 template <int MAXC>

@@ -1323,26 +1323,15 @@ inline cudaError_t smem_generations(size_t smem)
 
 // One kernel variant: launch / occupancy / shared-memory entry points for the
 // four chunk widths (index 0..3 = 1, 2, 4, 8 chunks per lane).
-template <class Pos, bool F32R>
-inline cudaError_t gen_entry(int op, int mc_index, const KParams* p, int grid, int block, size_t smem,
-                             cudaStream_t s, int* out)
+template <class Pos, bool F32R, int MCV>
+inline cudaError_t gen_entry_mc(int op, const KParams* p, int grid, int block, size_t smem, cudaStream_t s,
+                                int* out)
 {
-    switch (mc_index) {
-#define PSSO_GEN_CASE(IDX, MCV)                                                              \
-    case IDX:                                                                                \
-        if (op == 0) return launch_generations<Pos, F32R, MCV>(*p, grid, block, smem, s);    \
-        if (op == 1) return occupancy_generations<Pos, F32R, MCV>(block, smem, out);         \
-        if (op == 2) return smem_generations<Pos, F32R, MCV>(smem);                          \
-        *out = GenBound<MCV>::threads;                                                       \
-        return cudaSuccess;
-        PSSO_GEN_CASE(0, 1)
-        PSSO_GEN_CASE(1, 2)
-        PSSO_GEN_CASE(2, 4)
-        PSSO_GEN_CASE(3, 8)
-#undef PSSO_GEN_CASE
-    default:
-        return cudaErrorInvalidValue;
-    }
+    if (op == 0) return launch_generations<Pos, F32R, MCV>(*p, grid, block, smem, s);
+    if (op == 1) return occupancy_generations<Pos, F32R, MCV>(block, smem, out);
+    if (op == 2) return smem_generations<Pos, F32R, MCV>(smem);
+    *out = GenBound<MCV>::threads;
+    return cudaSuccess;
 }
 
 }  // namespace psso
