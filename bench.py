@@ -365,7 +365,8 @@ def main():
     st = psso.psso_stats(h)
     with ClockSampler(local) as clk:
         step_ms, kern_ms = timed_steps(h, args.steps, args.warmup)
-    rechecks = psso.psso_stats(h)["rechecks"]
+    st_end = psso.psso_stats(h)
+    rechecks, refinements = st_end["rechecks"], st_end["refinements"]
     best = psso.psso_best(h, 0)
     psso.psso_destroy(h)
     total = sum(step_ms)
@@ -448,6 +449,7 @@ def main():
         "fitness_evals_per_s": evals,
         "gpu_launches": 2 * args.steps,
         "rechecks_last_step": rechecks,
+        "refinements_last_step": refinements,
         "gbest": {"value": best[0], "index": best[1]},
         "fp64": fp64,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -168,6 +168,9 @@ typedef struct {
     int32_t threads_per_block;
     int32_t instances;
     int32_t reserved;
+    int64_t refinements;     /* rotated functions on the tensor-core pipeline: rows
+                                re-evaluated by the compensated FP32 rotation
+                                before any FP64 recheck                           */
 } psso_stats_t;
 
 /* Creates one swarm with the zero shift, FP64 lattice and FP64 precision,
@@ -313,12 +316,13 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
  * forms follow the usual z = M (x - o) convention).  DEVICE pointers, float32,
  * row-major: X (N*D), shift (D), rotation (D*D, M[j*D + k]), Z (N*D, out).
  * d = fl32(x - o) and M are split exactly into three BF16 parts each; the six
- * products above 2^-24 are accumulated in FP32 by tcgen05 MMAs (main part and
- * corrections in separate accumulators) and added.  Error model:
+ * products above 2^-24 are accumulated in FP32 by tcgen05 MMAs (the main part
+ * in three accumulators over K blocks dealt round robin, the corrections in a
+ * fourth) and added.  Error model:
  * |z~_j - sum_k M_jk d_k| <= c(Kp) * sum_k |M_jk| |d_k| + 2^-24 |z~_j|,
- * Kp = D rounded up to 64, c(Kp) = 1.05 (2^-22 1.04 (Kp/16)(1 + 5 2^-7)
- * + 1.03 2^-23 + 2.02 2^-24) when every MMA instruction errs by at most 2^-22
- * of its operand magnitudes.  1 <= N <= 2^24, 1 <= D <= 8192.  Allocates its
+ * Kp = D rounded up to 64, c(Kp) = 1.05 (2^-22 1.04 (4 ceil(Kp/192)
+ * + 5 (Kp/16) 2^-7) + 1.03 2^-23 + 5.12 2^-24) when every MMA instruction
+ * errs by at most 2^-22 of its operand magnitudes.  1 <= N <= 2^24, 1 <= D <= 8192.  Allocates its
  * operand planes for the call and synchronises `stream`.  PSSO_ERR_TIMEOUT if
  * a pipeline wait ran out (the device is left usable). */
 psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift, const float* rotation,

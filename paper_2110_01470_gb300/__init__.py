@@ -78,7 +78,8 @@ class psso_stats_t(ctypes.Structure):
                 ("updates", ctypes.c_int64), ("rechecks", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("instances", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("instances", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("refinements", ctypes.c_int64)]
 
 
 _lib = None

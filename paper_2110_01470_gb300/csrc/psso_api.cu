@@ -448,7 +448,9 @@ psso_status setup_tc(psso_ctx* h, size_t k)
                  omn = take((size_t)r.Jp * 4), odn = take((size_t)r.Np * 4), osame = take((size_t)N * 4),
                  opart = take((size_t)N * r.nJt * 16), ol1 = take((size_t)N * 4), ol2 = take((size_t)N * 4),
                  oz = take((size_t)2 * N * I.Dp * 8), oz0 = take((size_t)I.Dp * 8),
-                 octl = take(sizeof(rot::RotCtl));
+                 octl = take(sizeof(rot::RotCtl)), ol3 = take((size_t)N * 4),
+                 omh = take((size_t)D * D * 4), oml = take((size_t)D * D * 4),
+                 oz32 = take((size_t)2 * N * I.Dp * 4), oez = take((size_t)2 * N * I.Dp * 4);
     R.mem_bytes = align_up(off, 256);
     CUDA_TRY(cudaMalloc(&R.mem, R.mem_bytes));
     CUDA_TRY(cudaMemsetAsync(R.mem, 0, R.mem_bytes, h->stream));
@@ -464,6 +466,14 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     r.zbuf = reinterpret_cast<double*>(b + oz);
     r.zero64 = reinterpret_cast<const double*>(b + oz0);
     r.ctl = reinterpret_cast<rot::RotCtl*>(b + octl);
+    r.list3 = reinterpret_cast<int32_t*>(b + ol3);
+    R.Mh = reinterpret_cast<float*>(b + omh);
+    R.Ml = reinterpret_cast<float*>(b + oml);
+    r.Mh = R.Mh;
+    r.Ml = R.Ml;
+    r.z32 = reinterpret_cast<float*>(b + oz32);
+    r.ez32 = reinterpret_cast<float*>(b + oez);
+    R.M64 = reinterpret_cast<const double*>(h->arena + I.off_M64);
     r.inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev) + k;
     r.inst_w32 = I.w.empty() ? nullptr : reinterpret_cast<const float*>(h->arena + I.off_w32);
     R.M32 = reinterpret_cast<const float*>(h->arena + I.off_M32);
@@ -471,6 +481,7 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     cudaDeviceProp prop;
     CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
     R.z64_grid = 2 * prop.multiProcessorCount;
+    R.z32_grid = 8 * prop.multiProcessorCount;
     R.fix_grid = prop.multiProcessorCount;
     if (!tc::make_tmap_bf16(&R.tmA, r.A, r.Kp, 3 * r.Np) || !tc::make_tmap_bf16(&R.tmB, R.B, r.Kp, 3 * r.Jp))
         return fail(PSSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core operands");
@@ -860,6 +871,14 @@ psso_status psso_stats(psso_handle h, psso_stats_t* out)
             r += gb.total_rechecks;
     }
     out->rechecks = r;
+    int64_t refined = 0;
+    for (const auto& I : h->inst) {
+        if (!I.tc) continue;
+        unsigned long long v = 0;
+        if (cudaMemcpy(&v, &I.rh.dev.ctl->refined, sizeof v, cudaMemcpyDeviceToHost) == cudaSuccess)
+            refined += (int64_t)v;
+    }
+    out->refinements = refined;
     out->h2d_bytes = h->h2d;
     out->d2h_bytes = h->d2h;
     return PSSO_OK;

@@ -15,18 +15,28 @@
 //                    writes per-(particle, 128-column tile) partial sums.
 //   3. rot_decide    FP32 fitness and bound per particle; pBest update when
 //                    the interval decides it (Alg. 3, <=); else the particle
-//                    goes on the recheck list.
-//   4. rot_z64       FP64 z = M (x - o) of listed rows in the oracle's order
+//                    goes on list 1.
+//   4. rot_z32       refinement of list-1 rows: z by a compensated FP32 dot
+//                    product (Ogita, Rump, Oishi, "Accurate sum and dot
+//                    product", SISC 2005, Algorithm Dot2), error below
+//                    u |z| + 2 gamma_n^2 sum |M||d| -- some thousand times
+//                    tighter than the tensor-core bound.
+//   5. rot_fix32     fitness intervals from the refined z; decides the pBest
+//                    update, or the particle goes on list 3.
+//   6. rot_z64       FP64 z = M (x - o) of list-3 rows in the oracle's order
 //                    (k ascending, fma from +0), one thread per output.
-//   5. rot_fix       FP64 fitness of those rows (the oracle's summation) and
+//   7. rot_fix       FP64 fitness of those rows (the oracle's summation) and
 //                    the exact pBest decision.
-//   6. rot_argmin(0) gBest candidates (Alg. 4, lowest index): unique from the
+//   8. rot_argmin(0) gBest candidates (Alg. 4, lowest index): unique from the
 //                    intervals, or the pBests that can still be the minimum
-//                    go on a second list.
-//   7-8.             steps 4-5 for that list (pBest rows only).
-//   9. rot_argmin(1) the exact arg-min if needed, gBest record, log, gBest
+//                    go on list 2.
+//   9-10.            steps 6-7 for list 2 (pBest rows only).
+//  11. rot_argmin(1) the exact arg-min if needed, gBest record, log, gBest
 //                    row, generation counter + 1.
-// Steps 4-5 and 7-8 exit at once when their list is empty.
+// Steps 4-7 and 9-10 exit at once when their list is empty.  The refinement
+// exists because FP64 on this GPU runs at a small fraction of the FP32 rate:
+// one FP64 row costs D^2 FP64 fmas, the refinement about 14 D^2 FP32 ops.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cuda_bf16.h>
@@ -46,8 +56,10 @@ using tc::BN;
 __global__ void set_gen(RotCtl* ctl, long long g)
 {
     ctl->gen = g;
+    if (g == 0) ctl->refined = 0;    // counters restart with the swarm, like the gBest record's
     ctl->n1 = 0;
     ctl->n2 = 0;
+    ctl->n3 = 0;
     ctl->amb = 0;
     ctl->acc = 0;
     ctl->rck = 0;
@@ -147,6 +159,31 @@ __global__ void rot_update(const RotDev r)
 // persistent kernel): ellipsoid w z^2; Rastrigin z^2 + 20 sin^2(pi z);
 // Ackley z^2 and sin^2(pi z) (two sums).  Sums: 32 terms per column block,
 // then 4 blocks per tile, then the tiles (in rot_decide).
+__device__ __forceinline__ void term32(int fn, float zt, float ez, const float* w32, int j, float& s,
+                                       float& s2, float& e, float& eq)
+{
+    const float az = fabsf(zt);
+    const float xi = az + ez;
+    if (fn == FN_ELLIPSOID) {
+        const float w = __ldg(w32 + j);
+        const float tv = __fmul_rn(w, __fmul_rn(zt, zt));
+        s = __fadd_rn(s, tv);
+        e = __fadd_rn(e, 4.2f * 0x1p-24f * tv + 1.01f * w * (2.f * az + ez) * ez);
+    } else if (fn == FN_RASTRIGIN) {
+        const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
+        const float tv = __fmaf_rn(zt, zt, __fmul_rn(20.f, __fmul_rn(sn, sn)));
+        s = __fadd_rn(s, tv);
+        e = __fadd_rn(e, (2.f * SINPI32_ERR_U + 4.f) * 0x1p-24f * tv +
+                             1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ez);
+    } else {   // Ackley
+        s = __fadd_rn(s, __fmul_rn(zt, zt));
+        const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
+        s2 = __fadd_rn(s2, __fmul_rn(sn, sn));
+        e = __fadd_rn(e, 1.01f * (2.f * az + ez) * ez);
+        eq = __fadd_rn(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ez);
+    }
+}
+
 struct FitEpi {
     const RotDev* r;
     int fn, D;
@@ -160,27 +197,8 @@ struct FitEpi {
             const int j = j0 + t;
             if (j >= D) break;
             const float zt = z[t];
-            const float az = fabsf(zt);
-            const float ez = 1.01f * __fmaf_rn(r->zc * dn, __ldg(r->mnorm + j), 0x1p-24f * az);
-            const float xi = az + ez;
-            if (fn == FN_ELLIPSOID) {
-                const float w = __ldg(r->inst_w32 + j);
-                const float tv = __fmul_rn(w, __fmul_rn(zt, zt));
-                s = __fadd_rn(s, tv);
-                e = __fadd_rn(e, 4.2f * 0x1p-24f * tv + 1.01f * w * (2.f * az + ez) * ez);
-            } else if (fn == FN_RASTRIGIN) {
-                const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
-                const float tv = __fmaf_rn(zt, zt, __fmul_rn(20.f, __fmul_rn(sn, sn)));
-                s = __fadd_rn(s, tv);
-                e = __fadd_rn(e, (2.f * SINPI32_ERR_U + 4.f) * 0x1p-24f * tv +
-                                     1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ez);
-            } else {   // Ackley
-                s = __fadd_rn(s, __fmul_rn(zt, zt));
-                const float sn = sinpi_reduced_f32(__fsub_rn(zt, rintf(zt)));
-                s2 = __fadd_rn(s2, __fmul_rn(sn, sn));
-                e = __fadd_rn(e, 1.01f * (2.f * az + ez) * ez);
-                eq = __fadd_rn(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ez);
-            }
+            const float ez = 1.01f * __fmaf_rn(r->zc * dn, __ldg(r->mnorm + j), 0x1p-24f * fabsf(zt));
+            term32(fn, zt, ez, r->inst_w32, j, s, s2, e, eq);
         }
         acc = __fadd_rn(acc, s);
         acc2 = __fadd_rn(acc2, s2);
@@ -204,12 +222,12 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---- 3. FP32 decisions ------------------------------------------------------------
-// FP32 fitness and its bound from the tile sums (the rotated branches of the
-// FP32 path; csum = summation depth 32 + 4 + tiles, + 2).
-__device__ inline Fit32 rot_final(int fn, int D, float acc, float acc2, float accE, float rQ, int ntiles)
+// FP32 fitness and its bound from the sums of the terms (the rotated branches
+// of the FP32 path); csum = summation depth + 2 (GEMM epilogue: 32 + 4 +
+// tiles + 2).
+__device__ inline Fit32 rot_final(int fn, int D, float acc, float acc2, float accE, float rQ, float csum)
 {
     const float U = 0x1p-24f;
-    const float csum = 38.f + (float)ntiles;
     Fit32 f;
     if (fn != FN_ACKLEY) {
         f.f = acc;
@@ -252,7 +270,7 @@ __global__ void rot_decide(const RotDev r)
             ae = __fadd_rn(ae, __shfl_sync(0xffffffffu, p.z, t));
             aq = __fadd_rn(aq, __shfl_sync(0xffffffffu, p.w, t));
         }
-        const Fit32 f = rot_final(base_fn(r.fn), r.D, a, a2, ae, aq, r.nJt);
+        const Fit32 f = rot_final(base_fn(r.fn), r.D, a, a2, ae, aq, 38.f + (float)r.nJt);
         const float lo = __fsub_rd(f.f, f.E), hi = __fadd_ru(f.f, f.E);
         int accept = 0, write = 0, undecided = 0;
         if (g == 0) {
@@ -289,14 +307,195 @@ __global__ void rot_decide(const RotDev r)
     if (threadIdx.x == 0 && blk_acc) atomicAdd(&r.ctl->acc, blk_acc);
 }
 
+// ---- 4. refinement: compensated FP32 rotation of list-1 rows ---------------------------
+// d = x - o exactly as a float pair (TwoSum), M = Mh + Ml.  One warp per
+// output j, lane l taking k = l, l + 32, ... (coalesced rows of M): the Dot2
+// recurrence per lane (TwoProduct of Mh d_h, TwoSum into p, the rounding
+// errors and the cross terms Mh d_l + Ml d_h into s), then the 32 lane sums
+// merged by a TwoSum butterfly, z = p + s.  With n = ceil(D / 32) + 8 and
+// g = gamma_n: |z~ - z| <= 1.01 u |z~| + (2 g^2 + 4 u g + 2^-42) S, where
+// S = sum |M||d| <= S~ (1 + 2 gamma_D)(1 + 2^-22) from the FP32 sum S~ of
+// |Mh||d_h|; 2^-42 S also covers the oracle's own FP64 rounding of z.
+__global__ void __launch_bounds__(128) rot_z32(const RotDev r)
+{
+    __shared__ float dh[1024], dl[1024];
+    const InstDev& d = *r.inst;
+    const unsigned n = r.ctl->n1;
+    const int D = r.D;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nJb = (D + 127) / 128;
+    const float U = 0x1p-24f;
+    const float nl = (float)((D + 31) / 32 + 8);
+    const float gam = nl * U / (1.f - nl * U);
+    const float gD = (float)D * U / (1.f - (float)D * U);
+    const float cS = 1.01f * (2.f * gam * gam + 4.f * U * gam + 0x1p-42f) * (1.f + 2.f * gD) * (1.f + 0x1p-22f);
+    const long long items = (long long)n * 2 * nJb;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int jb = (int)(it % nJb);
+        const int row = (int)((it / nJb) & 1);
+        const long long e = it / nJb / 2;
+        const int32_t i = r.list1[e];
+        if (row == 1 && (d.pflag[i] & 1u)) continue;     // uniform over the block
+        const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
+        __syncthreads();
+        for (int k = threadIdx.x; k < D; k += blockDim.x) {
+            const float a = src[k], b = -__ldg(d.o32 + k);
+            const float sum = __fadd_rn(a, b);
+            const float bb = __fsub_rn(sum, a);
+            dh[k] = sum;
+            dl[k] = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+        }
+        __syncthreads();
+        const size_t o = (size_t)(2 * e + row) * d.Dp;
+        for (int t = 0; t < 32; ++t) {
+            const int j = jb * 128 + warp * 32 + t;
+            if (j >= D) {
+                if (j < d.Dp && lane == 0) {
+                    r.z32[o + j] = 0.f;
+                    r.ez32[o + j] = 0.f;
+                }
+                continue;
+            }
+            const float* mh = r.Mh + (size_t)j * D;
+            const float* ml = r.Ml + (size_t)j * D;
+            float p = 0.f, sc = 0.f, S = 0.f;
+            for (int k = lane; k < D; k += 32) {
+                const float a = __ldg(mh + k), b = dh[k];
+                const float h = __fmul_rn(a, b);
+                const float rr = __fmaf_rn(a, b, -h);                 // a b = h + rr exactly
+                const float tt = __fadd_rn(p, h);
+                const float bb = __fsub_rn(tt, p);
+                const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(tt, bb)), __fsub_rn(h, bb));   // p + h = tt + q
+                p = tt;
+                const float cross = __fmaf_rn(a, dl[k], __fmul_rn(__ldg(ml + k), b));
+                sc = __fadd_rn(sc, __fadd_rn(__fadd_rn(q, rr), cross));
+                S = __fmaf_rn(fabsf(a), fabsf(b), S);
+            }
+            for (int off = 16; off > 0; off >>= 1) {       // every lane ends with the same values
+                const float po = __shfl_xor_sync(0xffffffffu, p, off);
+                const float so = __shfl_xor_sync(0xffffffffu, sc, off);
+                const float Sq = __shfl_xor_sync(0xffffffffu, S, off);
+                const float tt = __fadd_rn(p, po);
+                const float bb = __fsub_rn(tt, p);
+                const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(tt, bb)), __fsub_rn(po, bb));
+                p = tt;
+                sc = __fadd_rn(__fadd_rn(sc, so), q);
+                S = __fadd_rn(S, Sq);
+            }
+            if (lane == 0) {
+                const float z = __fadd_rn(p, sc);
+                r.z32[o + j] = z;
+                r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
+            }
+        }
+    }
+}
+
+// ---- 5. decisions from the refined intervals ---------------------------------------------
+template <int MAXC>
+__device__ Fit32 fit_refined(const RotDev& r, const InstDev& d, const float* z, const float* ez, int lane)
+{
+    const int fn = base_fn(r.fn);
+    float s = 0.f, s2 = 0.f, e = 0.f, eq = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane + 32 * q;
+        if (c >= d.nchunks) continue;
+        float zv[4], ev[4];
+        ld4(z + 4 * c, zv);
+        ld4(ez + 4 * c, ev);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (4 * c + m < d.D) term32(fn, zv[m], ev[m], r.inst_w32, 4 * c + m, s, s2, e, eq);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off));
+        s2 = __fadd_rn(s2, __shfl_xor_sync(0xffffffffu, s2, off));
+        e = __fadd_rn(e, __shfl_xor_sync(0xffffffffu, e, off));
+        eq = __fadd_rn(eq, __shfl_xor_sync(0xffffffffu, eq, off));
+    }
+    return rot_final(fn, d.D, s, s2, e, eq, (float)(4 * MAXC + 5 + 2));
+}
+
+template <int MAXC>
+__device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int lane)
+{
+    const int32_t i = r.list1[e];
+    const int64_t g = r.ctl->gen;
+    const size_t ox = (size_t)(2 * e) * d.Dp, op = ox + d.Dp;
+    const Fit32 fx = fit_refined<MAXC>(r, d, r.z32 + ox, r.ez32 + ox, lane);
+    const float lox = __fsub_rd(fx.f, fx.E), hix = __fadd_ru(fx.f, fx.E);
+    float plo = d.plo[i], phi = d.phi[i];
+    const bool have_p = (d.pflag[i] & 1u) != 0;
+    if (!have_p) {       // the pBest's interval, tightened the same way (intersection of two bounds)
+        const Fit32 fp = fit_refined<MAXC>(r, d, r.z32 + op, r.ez32 + op, lane);
+        plo = fmaxf(plo, __fsub_rd(fp.f, fp.E));
+        phi = fminf(phi, __fadd_ru(fp.f, fp.E));
+    }
+    const int accept = hix < plo;
+    const int reject = lox > phi;
+    if (accept) {
+        const float* xr = static_cast<const float*>(d.X) + (int64_t)i * d.Dp;
+        float* prow = static_cast<float*>(d.P) + (int64_t)i * d.Dp;
+        for (int c = lane; c < d.nchunks; c += 32) {
+            float v[4];
+            ld4(xr + 4 * c, v);
+            st4(prow + 4 * c, v);
+        }
+    }
+    if (lane == 0) {
+        if (accept) {
+            d.plo[i] = lox;
+            d.phi[i] = hix;
+            d.pflag[i] = 0u;
+            d.pf64[i] = 0.0;
+            d.pver[i] = (uint32_t)g;
+            atomicAdd(&r.ctl->acc, 1ull);
+        } else {
+            d.plo[i] = plo;
+            d.phi[i] = phi;
+            if (!reject) r.list3[atomicAdd(&r.ctl->n3, 1u)] = i;
+        }
+        atomicAdd(&r.ctl->refined, have_p ? 1ull : 2ull);
+    }
+}
+
+__global__ void rot_fix32(const RotDev r)
+{
+    const int lane = threadIdx.x & 31;
+    const InstDev& d = *r.inst;
+    const unsigned n = r.ctl->n1;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < (long long)n;
+         e += nwarps) {
+        switch (d.maxc) {
+        case 1: fix32_one<1>(r, d, e, lane); break;
+        case 2: fix32_one<2>(r, d, e, lane); break;
+        case 4: fix32_one<4>(r, d, e, lane); break;
+        default: fix32_one<8>(r, d, e, lane); break;
+        }
+    }
+}
+
+// The float pair of M for the refinement (setup).
+__global__ void split_m64(const double* M64, long long DD, float* Mh, float* Ml)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < DD; q += (long long)gridDim.x * blockDim.x) {
+        const double m = M64[q];
+        const float h = __double2float_rn(m);
+        Mh[q] = h;
+        Ml[q] = __double2float_rn(m - (double)h);
+    }
+}
+
 // ---- 4/7. FP64 rotation of listed rows ------------------------------------------------
-// which = 1: entries of list1, row 2e = X_i and row 2e+1 = P_i when its FP64
+// which = 1: entries of list3, row 2e = X_i and row 2e+1 = P_i when its FP64
 // value is not known; which = 2: entries of list2, row 2e+1 = P_i.
 __global__ void rot_z64(const RotDev r, int which)
 {
     __shared__ double dsh[1024];
     const InstDev& d = *r.inst;
-    const unsigned n = which == 1 ? r.ctl->n1 : r.ctl->n2;
+    const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;
     const int D = r.D;
     const int nJb = (D + 127) / 128;
     const long long items = (long long)n * 2 * nJb;
@@ -304,7 +503,7 @@ __global__ void rot_z64(const RotDev r, int which)
         const int jb = (int)(it % nJb);
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
-        const int32_t i = which == 1 ? r.list1[e] : r.list2[e];
+        const int32_t i = which == 1 ? r.list3[e] : r.list2[e];
         const bool needed = which == 1 ? (row == 0 || !(d.pflag[i] & 1u)) : row == 1;
         if (!needed) continue;          // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
@@ -334,7 +533,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
     const double* zx = r.zbuf + (size_t)(2 * e) * d.Dp;
     const double* zp = zx + d.Dp;
     if (which == 1) {
-        const int32_t i = r.list1[e];
+        const int32_t i = r.list3[e];
         const bool have_p = (d.pflag[i] & 1u) != 0;
         const double fx = fit64_row<double>(hz, zx, false);
         const double fp = have_p ? d.pf64[i] : fit64_row<double>(hz, zp, false);
@@ -375,7 +574,7 @@ __global__ void rot_fix(const RotDev r, int which)
 {
     const int lane = threadIdx.x & 31;
     const InstDev& d = *r.inst;
-    const unsigned n = which == 1 ? r.ctl->n1 : r.ctl->n2;
+    const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < (long long)n;
          e += nwarps)
@@ -483,6 +682,7 @@ __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
         ctl->gen = g + 1;
         ctl->n1 = 0;
         ctl->n2 = 0;
+        ctl->n3 = 0;
         ctl->amb = 0;
         ctl->acc = 0;
         ctl->rck = 0;
@@ -498,6 +698,8 @@ cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s)
     rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / BN), 128, tc::SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
     rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
+    rot_z32<<<h.z32_grid, 128, 0, s>>>(r);
+    rot_fix32<<<h.fix_grid, 32 * wpb, 0, s>>>(r);
     rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 1);
     rot_fix<<<h.fix_grid, 32 * wpb, 0, s>>>(r, 1);
     rot_argmin<<<1, 1024, 0, s>>>(r, 0);
@@ -510,6 +712,10 @@ cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s)
 cudaError_t build_constants(const RotHost& h, cudaStream_t s)
 {
     const RotDev& r = h.dev;
+    const long long DD = (long long)r.D * r.D;
+    split_m64<<<(unsigned)std::min<long long>((DD + 255) / 256, 4096), 256, 0, s>>>(h.M64, DD, h.Mh, h.Ml);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     return tc::launch_split_matrix(h.M32, r.D, r.Jp, r.Kp, h.B, r.mnorm, s);
 }
 

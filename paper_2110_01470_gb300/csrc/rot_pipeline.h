@@ -13,10 +13,12 @@ namespace rot {
 // Per-instance control block in device memory.
 struct RotCtl {
     long long gen;                 // generation the next kernels run
-    unsigned n1, n2;               // recheck list lengths (decisions, arg-min)
+    unsigned n1, n2, n3;           // list lengths: undecided after the GEMM, arg-min
+                                   // candidates, undecided after the FP32 refinement
     int amb;                       // the arg-min needs the exact pass
     int status;                    // a tensor-core pipeline wait ran out
     unsigned long long acc, rck;   // pBest updates / FP64 evaluations this generation
+    unsigned long long refined;    // FP32 refinements (all generations)
     long long win_i;               // gBest of this generation
     double win_v;
     float win_lo, win_hi;
@@ -36,8 +38,13 @@ struct RotDev {
     float* dnorm;                  // [Np] bound on ||d_i||
     uint32_t* same;                // [N] x_i equals pBest_i bit for bit
     float4* part;                  // [N][nJt] tile sums (s1, s2, e1, e2)
-    int32_t* list1;                // [N] undecided pBest updates
+    int32_t* list1;                // [N] pBest updates undecided by the GEMM bounds
     int32_t* list2;                // [N] pBests that may be the minimum
+    int32_t* list3;                // [N] pBest updates undecided after the refinement
+    const float* Mh;               // [D][D] M = Mh + Ml (float pair, |M - Mh - Ml| <= 2^-48 |M|)
+    const float* Ml;
+    float* z32;                    // [2N][Dp] refined z rows of list1 particles
+    float* ez32;                   // [2N][Dp] their error bounds
     double* zbuf;                  // [2N][Dp] FP64 z rows of listed particles
     const double* zero64;          // [Dp] zeros
     RotCtl* ctl;
@@ -47,9 +54,12 @@ struct RotHost {
     RotDev dev;
     CUtensorMap tmA, tmB;
     __nv_bfloat16* B;              // [3][Jp][Kp] split planes of M32
+    float* Mh;                     // float pair of M (refinement)
+    float* Ml;
     const float* M32;
+    const double* M64;
     long long N;
-    int z64_grid, fix_grid;
+    int z64_grid, z32_grid, fix_grid;
     void* mem;                     // the one allocation holding the buffers above
     size_t mem_bytes;
 };

@@ -7,9 +7,12 @@
 // |v_m| <= 2^-8 |v| (1.01), |v_l| <= 2^-16 |v| (1.01); the third remainder is
 // exactly representable, so the split loses nothing).  Of the nine products
 // of the parts, the six above 2^-24 are formed:
-//     acc0 += d_h M_h                       (main accumulator)
+//     acc0[kb % 3] += d_h M_h               (main part; three accumulators, K
+//                                            blocks dealt round robin, so each
+//                                            chain is a third as long)
 //     acc1 += d_h M_m + d_m M_h + d_h M_l + d_l M_h + d_m M_m   (corrections)
-// and z = fl(acc0 + acc1).  BF16 x BF16 products are exact in FP32.
+// and z = fl(fl(fl(acc0[0] + acc0[1]) + acc0[2]) + acc1).  BF16 x BF16
+// products are exact in FP32.
 //
 // Operand layout in global memory (bf16, row-major, K contiguous):
 //     A: [3][Np][Kp]   part p of d for particle i at (p, i, k)
@@ -32,7 +35,8 @@ constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2;
 constexpr int TILE_BYTES = BM * BK * 2;                    // 16 KiB (BM == BN)
 constexpr int STAGE_BYTES = 6 * TILE_BYTES;                // 96 KiB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;    // + alignment slack
-constexpr int TMEM_COLS = 256;                             // acc0 | acc1
+constexpr int NCHAIN = 3;                                  // main-part accumulators (K split)
+constexpr int TMEM_COLS = 512;                             // acc0[0..2] | acc1
 constexpr long long WAIT_CYCLES = 4000000000LL;            // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -197,13 +201,17 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 constexpr float MMA_EPS = 0x1p-22f;
 
 // z error per unit of S = sum_k |M32_jk| |d_k| (S <= ||d|| ||M32_j||) for a
-// K extent of Kp: acc0 chain (Kp / 16 MMAs over products <= 1.03 S), acc1
-// chain (5 Kp / 16 MMAs over products <= 2^-7 1.03 S), the three dropped
-// products (<= 1.03 2^-23 S), d and M rounded to float (2 x 1.01 2^-24 S).
+// K extent of Kp: the acc0 chains (at most 4 ceil(Kp / 192) MMAs each, over
+// products summing to <= 1.03 S in all), the acc1 chain (5 Kp / 16 MMAs
+// over products <= 2^-7 1.03 S), the three dropped products (<= 1.03 2^-23
+// S), d and M rounded to float (2 x 1.01 2^-24 S), the three additions that
+// join the accumulators (3.1 2^-24 S).
 __host__ __device__ inline float z_err_per_s(int Kp)
 {
-    const float n0 = (float)(Kp / 16), n1 = 5.f * (float)(Kp / 16);
-    return 1.05f * (MMA_EPS * 1.04f * (n0 + n1 * 0x1p-7f) + 1.03f * 0x1p-23f + 2.02f * 0x1p-24f);
+    const int nkb = Kp / 64;
+    const float n0 = 4.f * (float)((nkb + NCHAIN - 1) / NCHAIN), n1 = 5.f * (float)(Kp / 16);
+    return 1.05f * (MMA_EPS * 1.04f * (n0 + n1 * 0x1p-7f) + 1.03f * 0x1p-23f + 2.02f * 0x1p-24f +
+                    3.1f * 0x1p-24f);
 }
 
 struct GemmArgs {
@@ -268,7 +276,7 @@ __device__ __forceinline__ bool gemm_tile(const CUtensorMap* tmA, const CUtensor
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        const uint32_t acc0 = tmem, acc1 = tmem + BN;
+        const uint32_t acc1 = tmem + NCHAIN * BN;
         bool ok = true;
         for (int kb = 0; kb < nkb && ok; ++kb) {
             const int s = kb % STAGES;
@@ -279,6 +287,7 @@ __device__ __forceinline__ bool gemm_tile(const CUtensorMap* tmA, const CUtensor
             }
             tc_fence_after();
             const uint32_t st = sbase + (uint32_t)(s * STAGE_BYTES);
+            const uint32_t acc0 = tmem + (uint32_t)((kb % NCHAIN) * BN);
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
                 const uint32_t off = (uint32_t)(ks * 32);   // 16 bf16 along K
@@ -288,9 +297,10 @@ __device__ __forceinline__ bool gemm_tile(const CUtensorMap* tmA, const CUtensor
                 const uint64_t bh = sdesc_sw128(st + 3 * TILE_BYTES + off);
                 const uint64_t bm = sdesc_sw128(st + 4 * TILE_BYTES + off);
                 const uint64_t bl = sdesc_sw128(st + 5 * TILE_BYTES + off);
-                const uint32_t accum = (kb | ks) ? 1u : 0u;
-                mma_bf16(acc0, ah, bh, idesc, accum);
-                mma_bf16(acc1, ah, bm, idesc, accum);
+                const uint32_t first0 = (kb < NCHAIN && ks == 0) ? 0u : 1u;   // chain's first MMA
+                const uint32_t first1 = (kb | ks) ? 1u : 0u;
+                mma_bf16(acc0, ah, bh, idesc, first0);
+                mma_bf16(acc1, ah, bm, idesc, first1);
                 mma_bf16(acc1, am, bh, idesc, 1u);
                 mma_bf16(acc1, ah, bl, idesc, 1u);
                 mma_bf16(acc1, al, bh, idesc, 1u);
@@ -309,11 +319,17 @@ __device__ __forceinline__ bool gemm_tile(const CUtensorMap* tmA, const CUtensor
     const bool good = !failed;
     if (good) {
         const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        const int chains = nkb < NCHAIN ? nkb : NCHAIN;   // chains that received products
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             float z0[32], z1[32];
             tmem_ld32(tmem + lane_base + (uint32_t)(32 * c), z0);
-            tmem_ld32(tmem + lane_base + (uint32_t)(BN + 32 * c), z1);
+            for (int ch = 1; ch < chains; ++ch) {
+                tmem_ld32(tmem + lane_base + (uint32_t)(ch * BN + 32 * c), z1);
+#pragma unroll
+                for (int t = 0; t < 32; ++t) z0[t] = __fadd_rn(z0[t], z1[t]);
+            }
+            tmem_ld32(tmem + lane_base + (uint32_t)(NCHAIN * BN + 32 * c), z1);
 #pragma unroll
             for (int t = 0; t < 32; ++t) z0[t] = __fadd_rn(z0[t], z1[t]);
             epi(c, z0);

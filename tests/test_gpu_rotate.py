@@ -15,8 +15,10 @@ pytestmark = pytest.mark.gpu
 
 
 def c_of(Kp):
-    n0, n1 = Kp // 16, 5 * (Kp // 16)
-    return 1.05 * (2.0 ** -22 * 1.04 * (n0 + n1 * 2.0 ** -7) + 1.03 * 2.0 ** -23 + 2.02 * 2.0 ** -24)
+    nkb = Kp // 64
+    n0, n1 = 4 * ((nkb + 2) // 3), 5 * (Kp // 16)
+    return 1.05 * (2.0 ** -22 * 1.04 * (n0 + n1 * 2.0 ** -7) + 1.03 * 2.0 ** -23 + 2.02 * 2.0 ** -24
+                   + 3.1 * 2.0 ** -24)
 
 
 def _rotate(lib, X32, o32, M32):
