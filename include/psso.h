@@ -171,6 +171,8 @@ typedef struct {
     int64_t refinements;     /* rotated functions on the tensor-core pipeline: rows
                                 re-evaluated by the compensated FP32 rotation
                                 before any FP64 recheck                           */
+    int64_t launches;        /* kernels this handle enqueued for psso_create,
+                                psso_run and psso_reset (graph nodes included)     */
 } psso_stats_t;
 
 /* Creates one swarm with the zero shift, FP64 lattice and FP64 precision,
@@ -327,6 +329,17 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
  * a pipeline wait ran out (the device is left usable). */
 psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift, const float* rotation,
                         float* Z, void* stream);
+
+/* Measurement aid for single-instance handles whose swarm runs on the
+ * tensor-core pipeline (rotated function, F32_RECHECK): runs `generations`
+ * generations exactly as psso_run would (same results), with a CUDA event
+ * between consecutive kernels on the handle's stream, and writes each
+ * kernel's mean duration in ms to ms[0..10] (update, GEMM + fitness epilogue,
+ * decisions, FP32 refinement rotation and decisions, FP64 rotation and
+ * decisions, arg-min, FP64 rotation and decisions of arg-min candidates,
+ * gBest); n >= 11.  The paper has no counterpart.  Synchronises.
+ * PSSO_ERR_UNSUPPORTED for a swarm on the persistent kernel. */
+psso_status psso_time_kernels(psso_handle h, int32_t instance, int32_t generations, float* ms, int32_t n);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);

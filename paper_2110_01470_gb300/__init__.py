@@ -79,7 +79,7 @@ class psso_stats_t(ctypes.Structure):
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("instances", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("refinements", ctypes.c_int64)]
+                ("refinements", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
         "psso_rotate": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_time_kernels": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32], st),
         "psso_polish": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                          ctypes.POINTER(ctypes.c_int32)], st),
         "psso_last_error": ([], ctypes.c_char_p),
@@ -323,6 +324,17 @@ def psso_rotate(N, D, X_ptr, shift_ptr, rotation_ptr, Z_ptr, stream=None):
     """Z = (X - o) M^T on the tensor cores (raw float32 device pointers).
     Synchronises ``stream``."""
     _check(load().psso_rotate(int(N), int(D), X_ptr, shift_ptr, rotation_ptr, Z_ptr, stream))
+
+
+PIPELINE_KERNELS = ("update", "gemm_fit", "decide", "z32", "fix32", "z64", "fix64", "argmin0",
+                    "z64_argmin", "fix64_argmin", "argmin1")
+
+
+def psso_time_kernels(h, instance=0, generations=10):
+    """Mean duration (ms) of each kernel of a tensor-pipeline generation."""
+    ms = (ctypes.c_float * 16)()
+    _check(load().psso_time_kernels(h, int(instance), int(generations), ctypes.addressof(ms), 16))
+    return dict(zip(PIPELINE_KERNELS, list(ms)[:len(PIPELINE_KERNELS)]))
 
 
 def psso_polish(h, instance=0, steps=20, lr=1e-3):

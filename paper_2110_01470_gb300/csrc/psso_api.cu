@@ -92,6 +92,7 @@ struct psso_ctx {
     int64_t gen = 0;
     int64_t evals = 0, updates = 0;
     int64_t h2d = 0, d2h = 0;
+    int64_t launches = 0;       // kernels this handle enqueued (graph nodes included)
     bool failed = false;
 };
 
@@ -411,12 +412,15 @@ psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
     p.g_end = g_end;
     p.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : (int64_t)50000000;
     p.fault_skip_rank = h->cfg.fault_skip_rank;
-    if (h->grid > 0)
+    if (h->grid > 0) {
         CUDA_TRY(launch_variant(h->variant, h->mc_index, p, h->grid, h->block, h->smem, h->stream));
+        ++h->launches;
+    }
     for (auto& I : h->inst) {
         if (!I.tc) continue;
         CUDA_TRY(rot::set_generation(I.rh, g_begin, h->stream));
-        for (int64_t g = g_begin; g <= g_end; ++g) CUDA_TRY(rot::enqueue_generation(I.rh, h->stream));
+        CUDA_TRY(rot::run_generations(I.rh, g_end - g_begin + 1, h->stream));
+        h->launches += 1 + rot::KERNELS_PER_GENERATION * (g_end - g_begin + 1);
     }
     return PSSO_OK;
 }
@@ -487,6 +491,7 @@ psso_status setup_tc(psso_ctx* h, size_t k)
         return fail(PSSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core operands");
     CUDA_TRY(rot::configure());
     CUDA_TRY(rot::build_constants(R, h->stream));
+    CUDA_TRY(rot::make_graphs(R));
     return PSSO_OK;
 }
 
@@ -879,6 +884,7 @@ psso_status psso_stats(psso_handle h, psso_stats_t* out)
             refined += (int64_t)v;
     }
     out->refinements = refined;
+    out->launches = h->launches;
     out->h2d_bytes = h->h2d;
     out->d2h_bytes = h->d2h;
     return PSSO_OK;
@@ -908,6 +914,43 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
     // value (and then always records that value).
     if (improved) *improved = (after.has64 && (!before.has64 || after.f64 < before.f64)) ? 1 : 0;
     return PSSO_OK;
+}
+
+psso_status psso_time_kernels(psso_handle h, int32_t instance, int32_t generations, float* ms, int32_t n)
+{
+    if (!h || !ms) return fail(PSSO_ERR_ARG, "handle or ms is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    if (generations < 1 || n < rot::KERNELS_PER_GENERATION)
+        return fail(PSSO_ERR_ARG, "need generations >= 1 and room for every kernel of a generation");
+    if (h->inst.size() != 1) return fail(PSSO_ERR_ARG, "psso_time_kernels needs a single-instance handle");
+    HostInst& I = h->inst[instance];
+    if (!I.tc) return fail(PSSO_ERR_UNSUPPORTED, "the instance runs on the persistent kernel (one launch per run)");
+    if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier");
+    if (h->gen + generations > 0xfffffff0LL) return fail(PSSO_ERR_ARG, "generation counter would exceed 2^32");
+    CUDA_TRY(cudaSetDevice(h->device));
+    constexpr int K = rot::KERNELS_PER_GENERATION;
+    cudaEvent_t ev[K + 1];
+    for (int q = 0; q <= K; ++q) CUDA_TRY(cudaEventCreate(&ev[q]));
+    std::vector<double> acc(K, 0.0);
+    psso_status st = PSSO_OK;
+    cudaError_t e = rot::set_generation(I.rh, h->gen + 1, h->stream);
+    for (int32_t g = 0; g < generations && e == cudaSuccess; ++g) {
+        e = rot::enqueue_generation_timed(I.rh, h->stream, ev);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
+        for (int q = 0; q < K && e == cudaSuccess; ++q) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+            acc[q] += t;
+        }
+    }
+    for (int q = 0; q <= K; ++q) cudaEventDestroy(ev[q]);
+    if (e != cudaSuccess) return fail(PSSO_ERR_CUDA, std::string("psso_time_kernels: ") + cudaGetErrorString(e));
+    h->gen += generations;
+    h->evals += I.pr.N * generations;
+    h->updates += I.pr.N * I.pr.D * generations;
+    h->launches += 1 + (int64_t)K * generations;
+    for (int q = 0; q < n; ++q) ms[q] = q < K ? (float)(acc[q] / generations) : 0.f;
+    return st;
 }
 
 struct SaveHeader {
@@ -974,8 +1017,10 @@ void psso_destroy(psso_handle h)
         cudaStreamSynchronize(h->stream);
         cudaFree(h->arena);
     }
-    for (auto& I : h->inst)
+    for (auto& I : h->inst) {
+        rot::destroy_graphs(I.rh);
         if (I.rh.mem) cudaFree(I.rh.mem);
+    }
     delete h;
 }
 

@@ -690,23 +690,90 @@ __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
 }
 
 // ---- host --------------------------------------------------------------------------------
+cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent_t* ev);
+
 cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s)
 {
+    return enqueue_generation_timed(h, s, nullptr);
+}
+
+// With ev (KERNELS_PER_GENERATION + 1 events), an event is recorded before
+// the first kernel and after each kernel.
+cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent_t* ev)
+{
+    int q = 0;
+    auto mark = [&] {
+        if (ev) cudaEventRecord(ev[q++], s);
+    };
+    mark();
     const RotDev& r = h.dev;
     const int N = (int)h.N;
     const int wpb = 8;
     rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
+    mark();
     rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / BN), 128, tc::SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
+    mark();
     rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
+    mark();
     rot_z32<<<h.z32_grid, 128, 0, s>>>(r);
+    mark();
     rot_fix32<<<h.fix_grid, 32 * wpb, 0, s>>>(r);
+    mark();
     rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 1);
+    mark();
     rot_fix<<<h.fix_grid, 32 * wpb, 0, s>>>(r, 1);
+    mark();
     rot_argmin<<<1, 1024, 0, s>>>(r, 0);
+    mark();
     rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 2);
+    mark();
     rot_fix<<<h.fix_grid, 32 * wpb, 0, s>>>(r, 2);
+    mark();
     rot_argmin<<<1, 1024, 0, s>>>(r, 1);
+    mark();
     return cudaGetLastError();
+}
+
+// The generation number lives in device memory, so one captured generation
+// replays unchanged; graphs are captured on a private stream and launched on
+// the caller's.
+cudaError_t make_graphs(RotHost& h)
+{
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        const int gens = which == 0 ? 1 : GRAPH_GENS;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int q = 0; q < gens && e == cudaSuccess; ++q) e = enqueue_generation(h, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(which == 0 ? &h.graph1 : &h.graphG, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    return e;
+}
+
+void destroy_graphs(RotHost& h)
+{
+    if (h.graph1) cudaGraphExecDestroy(h.graph1);
+    if (h.graphG) cudaGraphExecDestroy(h.graphG);
+    h.graph1 = h.graphG = nullptr;
+}
+
+cudaError_t run_generations(const RotHost& h, long long count, cudaStream_t s)
+{
+    for (; count >= GRAPH_GENS; count -= GRAPH_GENS) {
+        const cudaError_t e = cudaGraphLaunch(h.graphG, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (; count > 0; --count) {
+        const cudaError_t e = cudaGraphLaunch(h.graph1, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t build_constants(const RotHost& h, cudaStream_t s)

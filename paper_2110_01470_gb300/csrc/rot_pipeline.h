@@ -62,9 +62,19 @@ struct RotHost {
     int z64_grid, z32_grid, fix_grid;
     void* mem;                     // the one allocation holding the buffers above
     size_t mem_bytes;
+    cudaGraphExec_t graph1, graphG;  // one generation / GRAPH_GENS generations
 };
 
+constexpr int KERNELS_PER_GENERATION = 11;
+constexpr int GRAPH_GENS = 16;
+
 cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s);
+cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent_t* ev);
+// Captures the generation sequence into graphs of 1 and GRAPH_GENS generations.
+cudaError_t make_graphs(RotHost& h);
+void destroy_graphs(RotHost& h);
+// Enqueues `count` generations (graph replays) on s.
+cudaError_t run_generations(const RotHost& h, long long count, cudaStream_t s);
 cudaError_t build_constants(const RotHost& h, cudaStream_t s);
 cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s);
 cudaError_t configure();

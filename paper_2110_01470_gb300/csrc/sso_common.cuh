@@ -247,12 +247,12 @@ __device__ __forceinline__ void rot_matvec64(const Hot& in, const Pos (&x)[MAXC]
         for (int m = 0; m < 4; ++m) z[q][m] = zb.v[q][m];
 }
 
-template <class Pos, int MAXC>
-__device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
-                        int G)
+template <class Pos, int MAXC, bool ROT>
+__device__ __forceinline__ double fit64_impl(const Hot& in, const Pos (&x)[MAXC][4], int lane_g,
+                                             unsigned gmask, int G)
 {
     const int D = in.D, nch = in.nchunks;
-    const bool rot = is_rotated(in.fn);
+    const bool rot = ROT && is_rotated(in.fn);
     const int fn = base_fn(in.fn);
     double zr[MAXC][4];
     if (rot) rot_matvec64<Pos, MAXC>(in, x, lane_g, gmask, G, zr);
@@ -325,6 +325,28 @@ __device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], 
     const double B = expm1_f64(__dmul_rn(-0.2, A));
     const double C = expm1_f64(__dmul_rn(-2.0, __ddiv_rn(acc2, Dd)));
     return -__dadd_rn(__dmul_rn(20.0, B), __dmul_rn(0x1.5bf0a8b145769p+1, C));  // e
+}
+
+template <class Pos, int MAXC>
+__device__ __noinline__ double fit64_rotated(const Hot& in, const RowBuf<Pos, MAXC>& xb, int lane_g,
+                                             unsigned gmask, int G)
+{
+    return fit64_impl<Pos, MAXC, true>(in, xb.v, lane_g, gmask, G);
+}
+
+template <class Pos, int MAXC>
+__device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
+                                        int G)
+{
+    if (is_rotated(in.fn)) {
+        RowBuf<Pos, MAXC> xb;
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+        return fit64_rotated<Pos, MAXC>(in, xb, lane_g, gmask, G);
+    }
+    return fit64_impl<Pos, MAXC, false>(in, x, lane_g, gmask, G);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,12 +458,12 @@ __device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAX
         }
 }
 
-template <int MAXC>
-__device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
-                       int G)
+template <int MAXC, bool ROT>
+__device__ __forceinline__ Fit32 fit32_impl(const Hot& in, const float (&x)[MAXC][4], int lane_g,
+                                            unsigned gmask, int G)
 {
     const int D = in.D, nch = in.nchunks;
-    const bool rot = is_rotated(in.fn);
+    const bool rot = ROT && is_rotated(in.fn);
     const int fn = base_fn(in.fn);
     float zr[MAXC][4], ezr[MAXC][4];
     if (rot) rot_matvec32<MAXC>(in, x, lane_g, gmask, G, zr, ezr);
@@ -618,6 +640,31 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
     }
     r.E = __fadd_ru(r.E, 0x1p-40f * (acc + accE));
     return r;
+}
+
+// The rotated forms run out of line: the plain functions' code carries no
+// trace of them, and the row goes through a buffer so the caller's array
+// stays in registers.
+template <int MAXC>
+__device__ __noinline__ Fit32 fit32_rotated(const Hot& in, const RowBuf<float, MAXC>& xb, int lane_g,
+                                            unsigned gmask, int G)
+{
+    return fit32_impl<MAXC, true>(in, xb.v, lane_g, gmask, G);
+}
+
+template <int MAXC>
+__device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4], int lane_g, unsigned gmask,
+                                       int G)
+{
+    if (is_rotated(in.fn)) {
+        RowBuf<float, MAXC> xb;
+#pragma unroll
+        for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+        return fit32_rotated<MAXC>(in, xb, lane_g, gmask, G);
+    }
+    return fit32_impl<MAXC, false>(in, x, lane_g, gmask, G);
 }
 
 // ---------------------------------------------------------------------------

@@ -137,3 +137,27 @@ def test_polish_on_pipeline_instance(lib):
         assert v2 <= v1
     finally:
         lib.psso_destroy(h)
+
+
+def test_time_kernels_keeps_the_trajectory(lib):
+    p = workload.problem("rot_ellipsoid", 256, 80, seed=14, lattice="f32")
+    t1, t2 = 5, 7
+    h = lib.psso_create_ex([p], "f32", tensor_rotation=1)
+    try:
+        lib.psso_run(h, t1)
+        ms = lib.psso_time_kernels(h, 0, t2)
+        assert len(ms) == 11 and all(v > 0 for v in ms.values())
+        assert lib.psso_generation(h) == t1 + t2
+        X, P, pF = lib.psso_get_state(h, 0, p["N"], p["D"])
+        st = lib.psso_stats(h)
+    finally:
+        lib.psso_destroy(h)
+    r = _oracle(p, t1 + t2)
+    assert np.array_equal(X, r["X"]) and np.array_equal(P, r["P"])
+    assert st["launches"] == (1 + 11) + (1 + 11 * t1) + (1 + 11 * t2)
+    h = lib.psso_create_ex([p], "f32", tensor_rotation=-1)
+    try:
+        with pytest.raises(lib.PssoError):
+            lib.psso_time_kernels(h, 0, 2)
+    finally:
+        lib.psso_destroy(h)
