@@ -210,6 +210,9 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+GEMM_TRAFFIC_BYTES = {(8192, 1000): 56.755712e6 + 1.514752e6}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -238,8 +241,12 @@ def tensor_roofline(psso, problems, prec, sptr, gens=20):
     peaks, which = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     achieved = 2.0 * N * D * D / t / 1e12
+    # DRAM bytes per launch of rot_gemm_fit at N=8192, D=1000 from one ncu capture
+    # (profiles/rot_gemm_fit_rotated_d1000.md); valid for that shape and this kernel
+    traffic = GEMM_TRAFFIC_BYTES.get((N, D))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_algorithmic": 2 * 3 * (Np + Jp) * Kp,
             "kernel": "rot_gemm_fit (tcgen05 split-BF16 GEMM + fitness epilogue)",
             "kernel_ms_per_launch": ms["gemm_fit"],
             "executed_tflops": 6 * 2.0 * Np * Jp * Kp / t / 1e12,
