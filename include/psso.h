@@ -142,6 +142,13 @@ typedef struct {
                                    each generation as a kernel sequence around a
                                    tcgen05 tensor-core GEMM for z = M (x - o));
                                    1 = always; -1 = never (per-particle kernel)     */
+    int32_t batch_stream;       /* handles of many swarms: 0 = auto (16 or more
+                                   swarms that are not on the tensor-core pipeline
+                                   run each generation as one kernel per row-width
+                                   class over every particle of every swarm, then
+                                   one block per swarm for the gBest, replayed as
+                                   CUDA graphs); 1 = always; -1 = never (the
+                                   persistent kernel)                              */
 } psso_config;
 
 /* One log entry (psso_get_log). */

@@ -63,7 +63,8 @@ class psso_config(ctypes.Structure):
                 ("log_capacity", ctypes.c_int64), ("spin_limit", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("max_blocks", ctypes.c_int32),
                 ("fault_skip_rank", ctypes.c_int32), ("residency", ctypes.c_int32),
-                ("pipeline", ctypes.c_int32), ("tensor_rotation", ctypes.c_int32)]
+                ("pipeline", ctypes.c_int32), ("tensor_rotation", ctypes.c_int32),
+                ("batch_stream", ctypes.c_int32)]
 
 
 class psso_log_entry(ctypes.Structure):
@@ -170,7 +171,8 @@ def psso_create(fn, N, D, lb, ub, Cg, Cp, Cw, seed):
 
 def psso_create_ex(problems, precision=PSSO_PREC_F64, *, threads_per_block=0,
                    single_block_max=0, log_stride=0, log_capacity=0, spin_limit=0, stream=None,
-                   max_blocks=0, fault_skip_rank=0, residency=0, pipeline=0, tensor_rotation=0):
+                   max_blocks=0, fault_skip_rank=0, residency=0, pipeline=0, tensor_rotation=0,
+                   batch_stream=0):
     """``problems``: list of dicts with keys fn, N, D, lb, ub, Cg, Cp, Cw, seed and
     optional lattice, sid / stream_id, o / shift, w / weights, M / rotation."""
     arr = (psso_problem * len(problems))()
@@ -193,7 +195,7 @@ def psso_create_ex(problems, precision=PSSO_PREC_F64, *, threads_per_block=0,
         precision = PRECISION[precision]
     cfg = psso_config(int(precision), threads_per_block, single_block_max, log_stride,
                       log_capacity, spin_limit, stream, max_blocks, fault_skip_rank, residency,
-                      pipeline, tensor_rotation)
+                      pipeline, tensor_rotation, batch_stream)
     h = ctypes.c_void_p()
     _check(load().psso_create_ex(arr, len(problems), ctypes.byref(cfg), ctypes.byref(h)))
     return h

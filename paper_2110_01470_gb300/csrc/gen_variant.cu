@@ -33,6 +33,13 @@ cudaError_t PSSO_NAME(PSSO_VARIANT, PSSO_MC)(int op, const KParams* p, int grid,
     return gen_entry_mc<VPos, kF32R, PSSO_MC>(op, p, grid, block, smem, s, out);
 }
 
+#define PSSO_BNAME(v, m) PSSO_CAT3(bat_variant_, v, m)
+cudaError_t PSSO_BNAME(PSSO_VARIANT, PSSO_MC)(int op, const BatParams* p, int grid, int block, cudaStream_t s,
+                                               int* out)
+{
+    return bat_entry_mc<VPos, kF32R, PSSO_MC>(op, p, grid, block, s, out);
+}
+
 #if defined(PSSO_TRACE) && PSSO_VARIANT == 2 && PSSO_MC == 1
 extern "C" int psso_trace_dump(void* host, size_t bytes)
 {

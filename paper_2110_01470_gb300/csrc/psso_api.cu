@@ -65,7 +65,27 @@ struct HostInst {
            off_pflag = 0, off_grow = 0, off_rec = 0, off_rec2 = 0, off_gb = 0, off_gbrow = 0,
            off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0, off_M64 = 0, off_M32 = 0;
     bool tc = false;              // generations run by the tensor-core pipeline
+    bool bp = false;              // generations run by the batched throughput pipeline
     rot::RotHost rh{};
+};
+
+// The batched throughput pipeline of a handle.
+struct BatHost {
+    struct Class {
+        int mc_index = 0, G = 32, grid = 0;
+        int32_t* ids = nullptr;
+        int64_t* first = nullptr;
+        int32_t n = 0;
+        int64_t total = 0;
+    };
+    std::vector<Class> classes;
+    int32_t* all_ids = nullptr;   // every batched instance (arg-min blocks)
+    int32_t n_all = 0;
+    BatCounters* cnt = nullptr;
+    long long* gen = nullptr;
+    void* mem = nullptr;
+    cudaGraphExec_t graph1 = nullptr, graphG = nullptr;
+    static constexpr int GRAPH_GENS = 16;
 };
 
 }  // namespace
@@ -82,6 +102,7 @@ struct psso_ctx {
     int mc_index = 0;           // kernel width: up to 1, 2, 4, 8 chunks per lane
     size_t pos_size = 8;
     std::vector<HostInst> inst;
+    BatHost bat;
     std::vector<UnitDev> units;
     std::vector<int32_t> block_first;
     int grid = 0, block = 256;
@@ -169,7 +190,7 @@ psso_status plan(psso_ctx* h)
         I.G = std::min(32, pow2_ceil(I.nchunks));
         I.maxc = pow2_ceil((I.nchunks + 31) / 32);
         I.R = 1;
-        if (I.tc) continue;
+        if (I.tc || I.bp) continue;
         ++n_kernel;
         only = (int)k;
         unit_smem_max = std::max(unit_smem_max, align_up((size_t)I.Dp * h->pos_size, 16));
@@ -226,7 +247,7 @@ psso_status plan(psso_ctx* h)
         int64_t sumR = 0;
         for (size_t k = 0; k < h->inst.size(); ++k) {
             const HostInst& I = h->inst[k];
-            if (I.tc) {
+            if (I.tc || I.bp) {
                 R[k] = 1;               // no blocks of the persistent kernel
                 continue;
             }
@@ -259,7 +280,7 @@ psso_status plan(psso_ctx* h)
         for (size_t k = 0; k < h->inst.size(); ++k) {
             HostInst& I = h->inst[k];
             I.R = R[k];
-            if (I.tc) continue;
+            if (I.tc || I.bp) continue;
             const int ppp = (pipe ? nw - 1 : nw) * (32 / I.G);
             const int64_t passes = (I.pr.N + ppp - 1) / ppp;
             for (int r = 0; r < R[k]; ++r) {
@@ -416,6 +437,14 @@ psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
         CUDA_TRY(launch_variant(h->variant, h->mc_index, p, h->grid, h->block, h->smem, h->stream));
         ++h->launches;
     }
+    if (h->bat.n_all > 0) {
+        CUDA_TRY(launch_bat_set_gen(h->bat.gen, g_begin, h->stream));
+        int64_t count = g_end - g_begin + 1;
+        for (; count >= BatHost::GRAPH_GENS; count -= BatHost::GRAPH_GENS)
+            CUDA_TRY(cudaGraphLaunch(h->bat.graphG, h->stream));
+        for (; count > 0; --count) CUDA_TRY(cudaGraphLaunch(h->bat.graph1, h->stream));
+        h->launches += 1 + (int64_t)(h->bat.classes.size() + 2) * (g_end - g_begin + 1);
+    }
     for (auto& I : h->inst) {
         if (!I.tc) continue;
         CUDA_TRY(rot::set_generation(I.rh, g_begin, h->stream));
@@ -495,6 +524,104 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     return PSSO_OK;
 }
 
+cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s)
+{
+    const InstDev* inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
+    for (const auto& c : h->bat.classes) {
+        BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, h->bat.gen, h->bat.cnt};
+        const cudaError_t e = bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_bat_argmin(h->variant, inst, h->bat.all_ids, h->bat.n_all, h->bat.gen, h->bat.cnt, s);
+}
+
+// Classes of equal (lane-group width, chunks per lane), their device tables,
+// grid sizes from the occupancy of each step kernel, and the captured graphs.
+psso_status setup_bat(psso_ctx* h)
+{
+    BatHost& B = h->bat;
+    std::vector<std::vector<int32_t>> members;
+    std::vector<std::pair<int, int>> keys;   // (mc_index, G)
+    std::vector<int32_t> all;
+    for (size_t k = 0; k < h->inst.size(); ++k) {
+        const HostInst& I = h->inst[k];
+        if (!I.bp) continue;
+        const int mci = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
+        const std::pair<int, int> key(mci, I.G);
+        size_t c = 0;
+        while (c < keys.size() && keys[c] != key) ++c;
+        if (c == keys.size()) {
+            keys.push_back(key);
+            members.emplace_back();
+        }
+        members[c].push_back((int32_t)k);
+        all.push_back((int32_t)k);
+    }
+    B.n_all = (int32_t)all.size();
+    if (B.n_all == 0) return PSSO_OK;
+    size_t bytes = 0;
+    auto take = [&](size_t n) {
+        bytes = align_up(bytes, 256);
+        const size_t at = bytes;
+        bytes += n;
+        return at;
+    };
+    std::vector<size_t> oid(keys.size()), ofirst(keys.size());
+    for (size_t c = 0; c < keys.size(); ++c) {
+        oid[c] = take(members[c].size() * 4);
+        ofirst[c] = take((members[c].size() + 1) * 8);
+    }
+    const size_t oall = take(all.size() * 4), ocnt = take(h->inst.size() * sizeof(BatCounters)),
+                 ogen = take(sizeof(long long));
+    CUDA_TRY(cudaMalloc(&B.mem, bytes));
+    std::vector<char> host(bytes, 0);
+    char* base = static_cast<char*>(B.mem);
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
+    for (size_t c = 0; c < keys.size(); ++c) {
+        BatHost::Class cl;
+        cl.mc_index = keys[c].first;
+        cl.G = keys[c].second;
+        cl.n = (int32_t)members[c].size();
+        std::vector<int64_t> first(members[c].size() + 1, 0);
+        for (size_t q = 0; q < members[c].size(); ++q) first[q + 1] = first[q] + h->inst[members[c][q]].pr.N;
+        cl.total = first.back();
+        std::memcpy(host.data() + oid[c], members[c].data(), members[c].size() * 4);
+        std::memcpy(host.data() + ofirst[c], first.data(), first.size() * 8);
+        cl.ids = reinterpret_cast<int32_t*>(base + oid[c]);
+        cl.first = reinterpret_cast<int64_t*>(base + ofirst[c]);
+        int bps = 0;
+        CUDA_TRY(bat_call(h->variant, cl.mc_index, 1, nullptr, 0, 256, nullptr, &bps));
+        const int64_t groups_per_block = 256 / cl.G;
+        const int64_t need = (cl.total + groups_per_block - 1) / groups_per_block;
+        cl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(1, bps) * prop.multiProcessorCount));
+        B.classes.push_back(cl);
+    }
+    std::memcpy(host.data() + oall, all.data(), all.size() * 4);
+    B.all_ids = reinterpret_cast<int32_t*>(base + oall);
+    B.cnt = reinterpret_cast<BatCounters*>(base + ocnt);
+    B.gen = reinterpret_cast<long long*>(base + ogen);
+    CUDA_TRY(cudaMemcpy(B.mem, host.data(), bytes, cudaMemcpyHostToDevice));
+    h->h2d += (int64_t)bytes;
+    // graphs of 1 and GRAPH_GENS generations, captured on a private stream
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaSuccess;
+    for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+        const int gens = which == 0 ? 1 : BatHost::GRAPH_GENS;
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int q = 0; q < gens && e == cudaSuccess; ++q) e = enqueue_bat_generation(h, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(which == 0 ? &B.graph1 : &B.graphG, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+    }
+    cudaStreamDestroy(cs);
+    CUDA_TRY(e);
+    return PSSO_OK;
+}
+
 psso_status read_status(psso_ctx* h)
 {
     CUDA_TRY(cudaSetDevice(h->device));
@@ -545,6 +672,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     if (c.residency != 0 && c.residency != 2) return fail(PSSO_ERR_ARG, "residency must be 0 or 2");
     if (c.pipeline != 0 && c.pipeline != 2) return fail(PSSO_ERR_ARG, "pipeline must be 0 or 2");
     if (c.tensor_rotation < -1 || c.tensor_rotation > 1) return fail(PSSO_ERR_ARG, "tensor_rotation must be -1, 0 or 1");
+    if (c.batch_stream < -1 || c.batch_stream > 1) return fail(PSSO_ERR_ARG, "batch_stream must be -1, 0 or 1");
     for (int32_t k = 0; k < count; ++k) {
         psso_status st = check_problem(problems[k], c.precision, k);
         if (st != PSSO_OK) return st;
@@ -576,6 +704,12 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
         I.tc = h->precision == PSSO_PREC_F32_RECHECK && I.pr.fn >= PSSO_ROT_ELLIPSOID &&
                (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32));
+    }
+    {
+        int n_plain = 0;
+        for (const auto& I : h->inst) n_plain += I.tc ? 0 : 1;
+        const bool bat = c.batch_stream == 1 || (c.batch_stream == 0 && n_plain >= 16);
+        for (auto& I : h->inst) I.bp = bat && !I.tc;
     }
     psso_status st = plan(h);
     if (st != PSSO_OK) {
@@ -695,6 +829,8 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         st = setup_tc(h, k);
         if (st != PSSO_OK) return cleanup_fail(st);
     }
+    st = setup_bat(h);
+    if (st != PSSO_OK) return cleanup_fail(st);
     st = launch(h, 0, 0);
     if (st != PSSO_OK) return cleanup_fail(st);
     for (auto& I : h->inst) h->evals += I.pr.N;
@@ -1021,6 +1157,9 @@ void psso_destroy(psso_handle h)
         rot::destroy_graphs(I.rh);
         if (I.rh.mem) cudaFree(I.rh.mem);
     }
+    if (h->bat.graph1) cudaGraphExecDestroy(h->bat.graph1);
+    if (h->bat.graphG) cudaGraphExecDestroy(h->bat.graphG);
+    if (h->bat.mem) cudaFree(h->bat.mem);
     delete h;
 }
 

@@ -147,6 +147,34 @@ cudaError_t gen_call(int variant, int op, int mc_index, const KParams* p, int gr
                      size_t smem, cudaStream_t s, int* out);
 cudaError_t launch_best_f64(const InstDev* inst, int n_inst, int lattice, cudaStream_t s);
 
+// Batched throughput pipeline: one generation of many independent swarms as
+// one kernel per class of equal lane-group width G and chunks per lane (each
+// group of G lanes updates, evaluates and commits one particle, the particles
+// of every instance of the class in one flat range), then one block per
+// instance for the gBest.  Positions of instance ids[q] are particles
+// first[q] .. first[q+1]-1 of the class range.
+struct BatCounters {
+    unsigned long long acc, rck;   // pBest updates / FP64 evaluations this generation
+};
+struct BatParams {
+    const InstDev* inst;
+    const int32_t* ids;            // [n_ids] instance of each class entry
+    const int64_t* first;          // [n_ids + 1] prefix sums of N
+    int32_t n_ids, G;
+    int64_t total;                 // first[n_ids]
+    const long long* gen;          // generation being run (device)
+    BatCounters* cnt;              // [instances]
+};
+// op 0: launch bat_step over p (grid x block); op 1: occupancy (blocks per SM
+// into *out) for `block` threads.
+cudaError_t bat_call(int variant, int mc_index, int op, const BatParams* p, int grid, int block, cudaStream_t s,
+                     int* out);
+// One block per listed instance: gBest arg-min (exact lowest index), record,
+// log, gBest row; then the generation counter + 1 (last kernel of a generation).
+cudaError_t launch_bat_argmin(int variant, const InstDev* inst, const int32_t* ids, int n_ids, long long* gen,
+                              BatCounters* cnt, cudaStream_t s);
+cudaError_t launch_bat_set_gen(long long* gen, long long g, cudaStream_t s);
+
 cudaError_t launch_polish(const InstDev* inst, int k, int lattice, int owner_rank, int64_t g, int steps,
                           float lr, cudaStream_t s);
 

@@ -583,24 +583,6 @@ __global__ void rot_fix(const RotDev r, int which)
 
 
 // ---- 6/9. gBest --------------------------------------------------------------------------
-template <bool F32R>
-__device__ Cand block_reduce_cand(Cand c, Cand* sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
-    if (lane == 0) sh[w] = c;
-    __syncthreads();
-    if (w == 0) {
-        c = lane < nw ? sh[lane] : cand_none();
-        for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
-        if (lane == 0) sh[0] = c;
-    }
-    __syncthreads();
-    const Cand out = sh[0];
-    __syncthreads();
-    return out;
-}
-
 __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
 {
     __shared__ Cand sh[32];

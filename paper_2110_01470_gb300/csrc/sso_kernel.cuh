@@ -1323,6 +1323,84 @@ inline cudaError_t smem_generations(size_t smem)
 
 // One kernel variant: launch / occupancy / shared-memory entry points for the
 // four chunk widths (index 0..3 = 1, 2, 4, 8 chunks per lane).
+// Block-wide candidate reduction (every thread gets the result); sh holds one
+// Cand per warp.
+template <bool F32R>
+__device__ inline Cand block_reduce_cand(Cand c, Cand* sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
+    if (lane == 0) sh[w] = c;
+    __syncthreads();
+    if (w == 0) {
+        c = lane < nw ? sh[lane] : cand_none();
+        for (int off = 16; off > 0; off >>= 1) c = cand_merge<F32R>(c, cand_shfl(c, off));
+        if (lane == 0) sh[0] = c;
+    }
+    __syncthreads();
+    const Cand out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// Batched throughput pipeline, step kernel: every particle of the class range
+// by a group of G lanes -- the persistent kernel's Eq. 2.1 update, fitness
+// and pBest commit, reading the instance's gBest row from global memory.
+// Blocks per SM the step kernel is compiled for: narrow rows trade registers
+// (some spilled to L1) for the warps that hide the row loads' latency.
+template <int MC> struct BatBound { static constexpr int min_blocks = MC == 1 ? 4 : MC == 2 ? 3 : MC == 4 ? 2 : 1; };
+
+template <class Pos, bool F32R, int MC>
+__global__ void __launch_bounds__(256, BatBound<MC>::min_blocks) bat_step(const BatParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const int G = p.G;
+    const int lane_g = lane & (G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int64_t gpb = (int64_t)(blockDim.x / G);
+    const int64_t ngroups = gpb * gridDim.x;
+    const int64_t g = *p.gen;
+    for (int64_t gid = (int64_t)blockIdx.x * gpb + threadIdx.x / G; gid < p.total; gid += ngroups) {
+        // the class entry holding particle gid (first[] ascending)
+        int lo = 0, hi = p.n_ids - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(p.first + mid) <= gid) lo = mid;
+            else hi = mid - 1;
+        }
+        const int k = __ldg(p.ids + lo);
+        const int64_t i = gid - __ldg(p.first + lo);
+        const InstDev& d = p.inst[k];
+        const Hot in = hot_of(d);
+        View<Pos> v;
+        v.X = static_cast<Pos*>(d.X);
+        v.P = static_cast<Pos*>(d.P);
+        v.pf64 = d.pf64;
+        v.plo = d.plo;
+        v.phi = d.phi;
+        v.pver = d.pver;
+        v.pflag = d.pflag;
+        v.base = 0;
+        unsigned long long n_acc = 0, n_rck = 0;
+        PartState<Pos, MC> st;
+        particle_compute<Pos, F32R, MC>(in, v, static_cast<const Pos*>(d.gbrow), i, i, g, lane_g, gmask, st);
+        particle_commit<Pos, F32R, MC>(in, v, i, g, lane_g, gmask, st, n_acc, n_rck);
+        if (lane_g == 0 && (n_acc | n_rck)) {
+            if (n_acc) atomicAdd(&p.cnt[k].acc, n_acc);
+            if (n_rck) atomicAdd(&p.cnt[k].rck, n_rck);
+        }
+    }
+}
+
+template <class Pos, bool F32R, int MC>
+inline cudaError_t bat_entry_mc(int op, const BatParams* p, int grid, int block, cudaStream_t s, int* out)
+{
+    if (op == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_step<Pos, F32R, MC>, block, 0);
+    bat_step<Pos, F32R, MC><<<grid, block, 0, s>>>(*p);
+    return cudaGetLastError();
+}
+
 template <class Pos, bool F32R, int MCV>
 inline cudaError_t gen_entry_mc(int op, const KParams* p, int grid, int block, size_t smem, cudaStream_t s,
                                 int* out)
