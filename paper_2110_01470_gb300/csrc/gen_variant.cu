@@ -6,6 +6,9 @@
 //   PSSO_MC       1, 2, 4 or 8 chunks of 4 variables per lane
 // so that the twelve kernels compile in parallel.
 #include "sso_kernel.cuh"
+#if PSSO_MC == 8
+#include "bat_stream.cuh"
+#endif
 
 #if !defined(PSSO_VARIANT) || !defined(PSSO_MC)
 #error "gen_variant.cu is compiled with -DPSSO_VARIANT=v -DPSSO_MC=m"
@@ -37,6 +40,10 @@ cudaError_t PSSO_NAME(PSSO_VARIANT, PSSO_MC)(int op, const KParams* p, int grid,
 cudaError_t PSSO_BNAME(PSSO_VARIANT, PSSO_MC)(int op, const BatParams* p, int grid, int block, cudaStream_t s,
                                                int* out)
 {
+#if PSSO_MC == 8
+    // ops 2 / 3: the streaming kernel for wide unrotated rows (launch / occupancy)
+    if (op >= 2) return bat_stream_entry<VPos, kF32R>(op, p, grid, block, s, out);
+#endif
     return bat_entry_mc<VPos, kF32R, PSSO_MC>(op, p, grid, block, s, out);
 }
 

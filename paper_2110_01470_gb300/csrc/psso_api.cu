@@ -73,6 +73,7 @@ struct HostInst {
 struct BatHost {
     struct Class {
         int mc_index = 0, G = 32, grid = 0;
+        bool stream = false;       // wide unrotated rows: the streaming kernel
         int32_t* ids = nullptr;
         int64_t* first = nullptr;
         int32_t n = 0;
@@ -529,7 +530,8 @@ cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s)
     const InstDev* inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
     for (const auto& c : h->bat.classes) {
         BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, h->bat.gen, h->bat.cnt};
-        const cudaError_t e = bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
+        const cudaError_t e = c.stream ? bat_call(h->variant, 3, 2, &p, c.grid, 256, s, nullptr)
+                                       : bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
         if (e != cudaSuccess) return e;
     }
     return launch_bat_argmin(h->variant, inst, h->bat.all_ids, h->bat.n_all, h->bat.gen, h->bat.cnt, s);
@@ -541,12 +543,13 @@ psso_status setup_bat(psso_ctx* h)
 {
     BatHost& B = h->bat;
     std::vector<std::vector<int32_t>> members;
-    std::vector<std::pair<int, int>> keys;   // (mc_index, G)
+    std::vector<std::pair<int, int>> keys;   // (mc_index, G); mc_index 4 = streaming kernel
     std::vector<int32_t> all;
     for (size_t k = 0; k < h->inst.size(); ++k) {
         const HostInst& I = h->inst[k];
         if (!I.bp) continue;
-        const int mci = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
+        int mci = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
+        if (mci >= 2 && I.pr.fn < PSSO_ROT_ELLIPSOID) mci = 4;   // rows over 256 variables stream
         const std::pair<int, int> key(mci, I.G);
         size_t c = 0;
         while (c < keys.size() && keys[c] != key) ++c;
@@ -580,7 +583,8 @@ psso_status setup_bat(psso_ctx* h)
     CUDA_TRY(cudaGetDeviceProperties(&prop, h->device));
     for (size_t c = 0; c < keys.size(); ++c) {
         BatHost::Class cl;
-        cl.mc_index = keys[c].first;
+        cl.stream = keys[c].first == 4;
+        cl.mc_index = cl.stream ? 3 : keys[c].first;
         cl.G = keys[c].second;
         cl.n = (int32_t)members[c].size();
         std::vector<int64_t> first(members[c].size() + 1, 0);
@@ -591,8 +595,8 @@ psso_status setup_bat(psso_ctx* h)
         cl.ids = reinterpret_cast<int32_t*>(base + oid[c]);
         cl.first = reinterpret_cast<int64_t*>(base + ofirst[c]);
         int bps = 0;
-        CUDA_TRY(bat_call(h->variant, cl.mc_index, 1, nullptr, 0, 256, nullptr, &bps));
-        const int64_t groups_per_block = 256 / cl.G;
+        CUDA_TRY(bat_call(h->variant, cl.mc_index, cl.stream ? 3 : 1, nullptr, 0, 256, nullptr, &bps));
+        const int64_t groups_per_block = cl.stream ? 8 : 256 / cl.G;
         const int64_t need = (cl.total + groups_per_block - 1) / groups_per_block;
         cl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(1, bps) * prop.multiProcessorCount));
         B.classes.push_back(cl);

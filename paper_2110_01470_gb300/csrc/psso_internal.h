@@ -166,7 +166,8 @@ struct BatParams {
     BatCounters* cnt;              // [instances]
 };
 // op 0: launch bat_step over p (grid x block); op 1: occupancy (blocks per SM
-// into *out) for `block` threads.
+// into *out) for `block` threads; ops 2 / 3: the same for the streaming kernel
+// of wide unrotated rows (one warp per particle; mc_index 3 only).
 cudaError_t bat_call(int variant, int mc_index, int op, const BatParams* p, int grid, int block, cudaStream_t s,
                      int* out);
 // One block per listed instance: gBest arg-min (exact lowest index), record,
