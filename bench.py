@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--threads-per-block", type=int, default=0)
+    ap.add_argument("--threads-per-block", type=int, default=0,
+                    help="fixed block size (0 = the autotuner's choice)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1 = launch shape from psso_autotune (outside the timed steps)")
     ap.add_argument("--polish-steps", type=int, default=2,
                     help="timed runs with the gBest polish (workloads that define one)")
     return ap.parse_args()
@@ -409,9 +412,15 @@ def main():
         timed_launches[0] = psso.psso_stats(h)["launches"] - launches0
         return step_ms, kern_ms
 
+    def tuned_shape(precision):
+        """Launch shape from the library's autotuner (cached per process)."""
+        if args.threads_per_block or not args.autotune:
+            return {"threads_per_block": args.threads_per_block}, None
+        return psso.psso_autotune(problems, precision, generations=min(t, 200), stream=sptr)
+
     # --- main arm: the workload's precision -------------------------------------------
-    h = psso.psso_create_ex(problems, prec, stream=sptr,
-                            threads_per_block=args.threads_per_block)
+    shape, tune_report = tuned_shape(prec)
+    h = psso.psso_create_ex(problems, prec, stream=sptr, **shape)
     st = psso.psso_stats(h)
     with ClockSampler(local) as clk:
         step_ms, kern_ms = timed_steps(h, args.steps, args.warmup)
@@ -431,8 +440,8 @@ def main():
     # --- FP64-fitness arm on the same workload ------------------------------------------
     fp64 = None
     if prec != "f64" and args.fp64_steps > 0:
-        h = psso.psso_create_ex(problems, "f64", stream=sptr,
-                                threads_per_block=args.threads_per_block)
+        shape64, _ = tuned_shape("f64")
+        h = psso.psso_create_ex(problems, "f64", stream=sptr, **shape64)
         s64, k64 = timed_steps(h, args.fp64_steps, 1)
         b64 = psso.psso_best(h, 0)
         psso.psso_destroy(h)
@@ -456,8 +465,8 @@ def main():
     for k in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = psso.psso_create_ex(problems, prec, stream=sptr,
-                                threads_per_block=args.threads_per_block)
+        shape_e, _ = tuned_shape(prec)        # the user's call; answered from the cache
+        h = psso.psso_create_ex(problems, prec, stream=sptr, **shape_e)
         psso.psso_run(h, t)
         v, i, row = psso.psso_best(h, 0, problems[0]["D"])
         s = psso.psso_stats(h)
@@ -504,6 +513,7 @@ def main():
         "refinements_last_step": refinements,
         "gbest": {"value": best[0], "index": best[1]},
         "fp64": fp64,
+        "autotune": tune_report,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roofline,

@@ -149,6 +149,10 @@ typedef struct {
                                    one block per swarm for the gBest, replayed as
                                    CUDA graphs); 1 = always; -1 = never (the
                                    persistent kernel)                              */
+    int32_t batch_blocks_per_sm;/* batched pipeline: resident blocks per SM of each
+                                   step kernel's grid (0 = the occupancy maximum;
+                                   larger values are clamped to it)                 */
+    int32_t reserved;           /* must be 0                                        */
 } psso_config;
 
 /* One log entry (psso_get_log). */
@@ -174,7 +178,8 @@ typedef struct {
     int32_t blocks;          /* blocks of the persistent launch                     */
     int32_t threads_per_block;
     int32_t instances;
-    int32_t reserved;
+    int32_t batch_classes;   /* step kernels per generation of the batched pipeline
+                                (0 when the handle does not use it)               */
     int64_t refinements;     /* rotated functions on the tensor-core pipeline: rows
                                 re-evaluated by the compensated FP32 rotation
                                 before any FP64 recheck                           */
@@ -347,6 +352,36 @@ psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift
  * gBest); n >= 11.  The paper has no counterpart.  Synchronises.
  * PSSO_ERR_UNSUPPORTED for a swarm on the persistent kernel. */
 psso_status psso_time_kernels(psso_handle h, int32_t instance, int32_t generations, float* ms, int32_t n);
+
+/* Result of psso_autotune. */
+typedef struct {
+    int32_t candidates;          /* configurations timed (0: answered from the cache) */
+    int32_t threads_per_block;   /* chosen psso_config.threads_per_block              */
+    int32_t batch_blocks_per_sm; /* chosen psso_config.batch_blocks_per_sm            */
+    int32_t reserved;
+    double best_ms;              /* mean ms per generation, chosen configuration      */
+    double default_ms;           /* mean ms per generation, configuration as given    */
+} psso_tune_report;
+
+/* Launch-shape autotuner (the paper has no counterpart; its kernels use one
+ * fixed shape).  Creates a scratch handle for each candidate configuration of
+ * `problems`, runs 3 warm-up generations and then times `generations` (1 ..
+ * 100000) generations with CUDA events on a private stream, and writes into
+ * `tuned` a copy of `cfg` (NULL = defaults) with the fastest candidate's
+ * shape:
+ *   - threads_per_block (particles per block of the persistent kernel), when
+ *     some swarm runs on it;
+ *   - batch_blocks_per_sm (grid of the batched pipeline's step kernels), when
+ *     the handle uses that pipeline.
+ * The given configuration is always a candidate, so the chosen one is never
+ * slower in the sweep.  Swarms on the tensor-core pipeline have fixed tile
+ * shapes and add no candidates.  The launch shape never changes results, so
+ * a handle made with `tuned` computes exactly what one made with `cfg` does.
+ * Results are cached per process by (problem shapes, functions, lattice,
+ * configuration): a repeated call times nothing.  `report` may be NULL.
+ * Allocates and frees device memory for each candidate; synchronises. */
+psso_status psso_autotune(const psso_problem* problems, int32_t count, const psso_config* cfg,
+                          int32_t generations, psso_config* tuned, psso_tune_report* report);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);

@@ -64,7 +64,14 @@ class psso_config(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("max_blocks", ctypes.c_int32),
                 ("fault_skip_rank", ctypes.c_int32), ("residency", ctypes.c_int32),
                 ("pipeline", ctypes.c_int32), ("tensor_rotation", ctypes.c_int32),
-                ("batch_stream", ctypes.c_int32)]
+                ("batch_stream", ctypes.c_int32), ("batch_blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class psso_tune_report(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("batch_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 class psso_log_entry(ctypes.Structure):
@@ -79,7 +86,7 @@ class psso_stats_t(ctypes.Structure):
                 ("updates", ctypes.c_int64), ("rechecks", ctypes.c_int64),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64),
                 ("blocks", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("instances", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("instances", ctypes.c_int32), ("batch_classes", ctypes.c_int32),
                 ("refinements", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
@@ -133,6 +140,9 @@ def load(path: str = LIB_PATH):
         "psso_time_kernels": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32], st),
         "psso_polish": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                          ctypes.POINTER(ctypes.c_int32)], st),
+        "psso_autotune": ([ctypes.POINTER(psso_problem), ctypes.c_int32,
+                           ctypes.POINTER(psso_config), ctypes.c_int32,
+                           ctypes.POINTER(psso_config), ctypes.POINTER(psso_tune_report)], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -169,12 +179,25 @@ def psso_create(fn, N, D, lb, ub, Cg, Cp, Cw, seed):
     return h
 
 
-def psso_create_ex(problems, precision=PSSO_PREC_F64, *, threads_per_block=0,
-                   single_block_max=0, log_stride=0, log_capacity=0, spin_limit=0, stream=None,
-                   max_blocks=0, fault_skip_rank=0, residency=0, pipeline=0, tensor_rotation=0,
-                   batch_stream=0):
-    """``problems``: list of dicts with keys fn, N, D, lb, ub, Cg, Cp, Cw, seed and
-    optional lattice, sid / stream_id, o / shift, w / weights, M / rotation."""
+_CONFIG_KEYS = ("threads_per_block", "single_block_max", "log_stride", "log_capacity",
+                "spin_limit", "stream", "max_blocks", "fault_skip_rank", "residency", "pipeline",
+                "tensor_rotation", "batch_stream", "batch_blocks_per_sm")
+
+
+def _config(precision, opts):
+    if isinstance(precision, str):
+        precision = PRECISION[precision]
+    bad = set(opts) - set(_CONFIG_KEYS)
+    if bad:
+        raise TypeError(f"unknown configuration fields {sorted(bad)}")
+    cfg = psso_config()
+    cfg.precision = int(precision)
+    for k, v in opts.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _problems(problems):
     arr = (psso_problem * len(problems))()
     keep = []
     for k, p in enumerate(problems):
@@ -191,14 +214,38 @@ def psso_create_ex(problems, precision=PSSO_PREC_F64, *, threads_per_block=0,
                               float(p["Cp"]), float(p["Cw"]), int(p["seed"]),
                               int(p.get("sid", p.get("stream_id", 0))), 0, _ptr(o), _ptr(w),
                               _ptr(M))
-    if isinstance(precision, str):
-        precision = PRECISION[precision]
-    cfg = psso_config(int(precision), threads_per_block, single_block_max, log_stride,
-                      log_capacity, spin_limit, stream, max_blocks, fault_skip_rank, residency,
-                      pipeline, tensor_rotation, batch_stream)
+    return arr, keep
+
+
+def psso_create_ex(problems, precision=PSSO_PREC_F64, **config):
+    """``problems``: list of dicts with keys fn, N, D, lb, ub, Cg, Cp, Cw, seed and
+    optional lattice, sid / stream_id, o / shift, w / weights, M / rotation.
+    ``config``: any psso_config field by name (threads_per_block, log_stride,
+    log_capacity, stream, batch_blocks_per_sm, ...)."""
+    arr, keep = _problems(problems)
+    cfg = _config(precision, config)
     h = ctypes.c_void_p()
     _check(load().psso_create_ex(arr, len(problems), ctypes.byref(cfg), ctypes.byref(h)))
     return h
+
+
+def psso_autotune(problems, precision=PSSO_PREC_F64, generations=200, **config):
+    """Launch-shape autotuner: returns (fields, report) where ``fields`` is a
+    dict of the tuned psso_config fields (threads_per_block,
+    batch_blocks_per_sm) to pass on to psso_create_ex, and ``report`` a dict
+    (candidates, best_ms, default_ms per generation)."""
+    arr, keep = _problems(problems)
+    cfg = _config(precision, config)
+    out = psso_config()
+    rep = psso_tune_report()
+    _check(load().psso_autotune(arr, len(problems), ctypes.byref(cfg), int(generations),
+                                ctypes.byref(out), ctypes.byref(rep)))
+    fields = {"threads_per_block": out.threads_per_block,
+              "batch_blocks_per_sm": out.batch_blocks_per_sm}
+    report = {"candidates": rep.candidates, "threads_per_block": rep.threads_per_block,
+              "batch_blocks_per_sm": rep.batch_blocks_per_sm, "best_ms": rep.best_ms,
+              "default_ms": rep.default_ms}
+    return fields, report
 
 
 def psso_run(h, generations):

@@ -53,9 +53,17 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     jobs.sort(key=lambda j: (j[0] != variant_src, -int(j[1][-1]) if j[0] == variant_src else 0))
     exe = nvcc()
 
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
+    newest_header = max(os.path.getmtime(f) for f in headers)
+
     def compile_one(job):
         src, name, defs = job
         obj = os.path.join(OBJDIR, name + ".o")
+        # an object is current when newer than its source and every header
+        if not force and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            return obj
         cmd = [exe, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:

@@ -596,6 +596,7 @@ psso_status setup_bat(psso_ctx* h)
         cl.first = reinterpret_cast<int64_t*>(base + ofirst[c]);
         int bps = 0;
         CUDA_TRY(bat_call(h->variant, cl.mc_index, cl.stream ? 3 : 1, nullptr, 0, 256, nullptr, &bps));
+        if (h->cfg.batch_blocks_per_sm > 0) bps = std::min(bps, (int)h->cfg.batch_blocks_per_sm);
         const int64_t groups_per_block = cl.stream ? 8 : 256 / cl.G;
         const int64_t need = (cl.total + groups_per_block - 1) / groups_per_block;
         cl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(1, bps) * prop.multiProcessorCount));
@@ -677,6 +678,9 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     if (c.pipeline != 0 && c.pipeline != 2) return fail(PSSO_ERR_ARG, "pipeline must be 0 or 2");
     if (c.tensor_rotation < -1 || c.tensor_rotation > 1) return fail(PSSO_ERR_ARG, "tensor_rotation must be -1, 0 or 1");
     if (c.batch_stream < -1 || c.batch_stream > 1) return fail(PSSO_ERR_ARG, "batch_stream must be -1, 0 or 1");
+    if (c.batch_blocks_per_sm < 0 || c.batch_blocks_per_sm > 64)
+        return fail(PSSO_ERR_ARG, "batch_blocks_per_sm must be in [0, 64]");
+    if (c.reserved != 0) return fail(PSSO_ERR_ARG, "psso_config.reserved must be 0");
     for (int32_t k = 0; k < count; ++k) {
         psso_status st = check_problem(problems[k], c.precision, k);
         if (st != PSSO_OK) return st;
@@ -1009,6 +1013,7 @@ psso_status psso_stats(psso_handle h, psso_stats_t* out)
     out->blocks = h->grid;
     out->threads_per_block = h->block;
     out->instances = (int32_t)h->inst.size();
+    out->batch_classes = (int32_t)h->bat.classes.size();
     int64_t r = 0;
     for (const auto& I : h->inst) {
         GBestDev gb;
