@@ -1,5 +1,5 @@
 // bat_stream.cuh -- streaming step kernel of the batched throughput pipeline
-// for wide rows (more than 256 variables, unrotated functions).
+// for wide rows (more than 128 variables, unrotated functions).
 //
 // One warp per particle walks its row one 32-chunk slice at a time: Eq. 2.1
 // for the slice (the same draws as the persistent kernel), the slice stored,
@@ -193,14 +193,16 @@ __global__ void __launch_bounds__(256, 3) bat_stream(const BatParams p)
                 if (g == 0) {
                     fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
                 } else {
-                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
-                    uint4 fb = make_uint4(0u, 0u, 0u, 0u);
-                    if (sizeof(Pos) == 4)
-                        fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+                    // the slice's loads first: the draws below do not depend on
+                    // them and cover their latency
                     Pos xo[4], po[4], go[4];
                     ld4(xr + 4 * c, xo);
                     ld4(prow + 4 * c, po);
                     ld4(gs + 4 * c, go);
+                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+                    uint4 fb = make_uint4(0u, 0u, 0u, 0u);
+                    if (sizeof(Pos) == 4)
+                        fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
                     uint32_t nf = 0;
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
@@ -229,13 +231,17 @@ __global__ void __launch_bounds__(256, 3) bat_stream(const BatParams p)
                 }
                 st4(xr + 4 * c, x);
             }
-            // fitness terms of the slice
-            Val dv[4];
+            // fitness terms of the slice (the shift is padded to Dp values)
+            Val dv[4], ov[4] = {Val(0), Val(0), Val(0), Val(0)};
+            if (has) {
+                if constexpr (F32R) ld4(in.o32 + 4 * c, ov);
+                else ld4(in.o64 + 4 * c, ov);
+            }
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int j = 4 * c + m;
-                if constexpr (F32R) dv[m] = (has && j < in.D) ? __fsub_rn((float)x[m], __ldg(in.o32 + j)) : 0.f;
-                else dv[m] = (has && j < in.D) ? __dsub_rn((double)x[m], __ldg(in.o64 + j)) : 0.0;
+                if constexpr (F32R) dv[m] = (has && j < in.D) ? __fsub_rn((float)x[m], ov[m]) : 0.f;
+                else dv[m] = (has && j < in.D) ? __dsub_rn((double)x[m], ov[m]) : 0.0;
             }
             Val next = Val(0);
             if (fn == FN_ROSENBROCK) {

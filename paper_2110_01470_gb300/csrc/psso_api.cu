@@ -549,7 +549,10 @@ psso_status setup_bat(psso_ctx* h)
         const HostInst& I = h->inst[k];
         if (!I.bp) continue;
         int mci = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
-        if (mci >= 2 && I.pr.fn < PSSO_ROT_ELLIPSOID) mci = 4;   // rows over 256 variables stream
+        // Unrotated rows over 128 variables (one particle per warp) run on the
+        // streaming kernel: it holds one 32-chunk slice in registers instead
+        // of the whole row, so more warps fit on an SM.
+        if (mci >= 1 && I.pr.fn < PSSO_ROT_ELLIPSOID) mci = 4;
         const std::pair<int, int> key(mci, I.G);
         size_t c = 0;
         while (c < keys.size() && keys[c] != key) ++c;

@@ -72,6 +72,7 @@ __device__ __forceinline__ int slot_of(int64_t g) { return (int)(g % SLOTS); }
 // Named block barriers (0 is __syncthreads): producers arrive, consumers wait.
 constexpr int BAR_VERDICT = 1;   // control warp -> compute warps: gBest of g-1 decided
 constexpr int BAR_CAND = 2;      // compute warps -> control warp: candidates of g written
+constexpr int BAR_PUB = 3;       // control warp -> compute warps: winner of g published
 __device__ __forceinline__ void bar_arrive(int id, int n)
 {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -723,10 +724,11 @@ __device__ __noinline__ Cand step_c_exact(const InstDev& in, const UnitDev un, c
 // Step C (warp 0): the unit's winner from the per-warp candidates.
 template <class Pos, bool F32R>
 __device__ __forceinline__ Winner step_c(const InstDev& in, const UnitDev& un, const View<Pos>& v,
-                                         BlockShared& sh)
+                                         BlockShared& sh, int64_t g)
 {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const Cand c = lane < nw ? sh.warp_cand[lane] : cand_none();   // unused slots hold none
+    trace_point(g, 6);
     int top = 1;
     while (2 * top < nw) top <<= 1;                 // lanes >= nw hold nothing
     unsigned long long acc = lane < nw ? sh.warp_acc[lane] : 0ull;
@@ -737,12 +739,15 @@ __device__ __forceinline__ Winner step_c(const InstDev& in, const UnitDev& un, c
     }
     acc = __shfl_sync(0xffffffffu, acc, 0);
     rck = __shfl_sync(0xffffffffu, rck, 0);
+    trace_point(g, 7);
     Cand r = cand_warp_reduce<F32R>(c, 1, top);
+    trace_point(g, 10);
     if (F32R && r.l2 <= r.mh) {
         unsigned long long extra = 0;
         r = step_c_exact<Pos>(in, un, v, r.mh, &extra);
         rck += extra;
     }
+    trace_point(g, 11);
     Winner w;
     w.idx = r.i;
     w.ver = r.ver;
@@ -1100,10 +1105,13 @@ __device__ Cand unit_spec(const KParams& p, const InstDev& in, const UnitDev& un
 // Warp-specialised pipeline for a block that owns one unit of a multi-block
 // instance with at most one particle per compute group.  Warp 0 (control)
 // runs steps C and D of generation g and step A of g (reading every block's
-// record); meanwhile warps 1.. (compute) already evaluate generation g+1 with
-// the gBest row they hold.  When the verdict of step A says the row was
-// current, their results are committed as computed; otherwise they are
-// recomputed.  Two named barriers carry the hand-offs.
+// record); once it has published, warps 1.. (compute) already evaluate
+// generation g+1 with the gBest row they hold while the records travel.  When
+// the verdict of step A says the row was current, their results are committed
+// as computed; otherwise they are recomputed.  The compute warps start only
+// after the publication so that steps C and D, on the critical path of every
+// block, do not share issue slots with them.  Three named barriers carry the
+// hand-offs.
 template <class Pos, bool F32R, int MAXC>
 __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const UnitDev& un,
                                const View<Pos>& v, Pos* gs, int slot, BlockShared& sh)
@@ -1126,10 +1134,11 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
             trace_point(g, 2);
             if (lane == 0) { sh.warp_cand[0] = cand_none(); sh.warp_acc[0] = 0; sh.warp_rck[0] = 0; }
             __syncwarp();
-            const Winner w = step_c<Pos, F32R>(desc, un, v, sh);
+            const Winner w = step_c<Pos, F32R>(desc, un, v, sh, g);
             trace_point(g, 3);
             step_d_publish<Pos>(p, desc, un, v, w, g);
             trace_point(g, 4);
+            if (g < p.g_end) bar_arrive(BAR_PUB, nth);
         }
         return;
     }
@@ -1139,6 +1148,7 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
     const bool have = gr.gid < n;
     const int64_t i = un.i0 + gr.gid, e = i - v.base;
     for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
+        if (g > p.g_begin) bar_sync(BAR_PUB, nth);
         PartState<Pos, MAXC> st;
         if (have) particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
         if (threadIdx.x == 32) trace_point(g, 7);
@@ -1250,7 +1260,7 @@ __global__ void __launch_bounds__(GenBound<MC>::threads) sso_generations(const K
             __syncthreads();
             trace_point(g, 2);
             if (warp == 0) {
-                const Winner w = step_c<Pos, F32R>(in, un, v, sh);
+                const Winner w = step_c<Pos, F32R>(in, un, v, sh, g);
                 trace_point(g, 3);
                 if (in.R == 1) step_d_local<Pos>(in, v, w, gs, slot, g, sh);
                 else step_d_publish<Pos>(p, in, un, v, w, g);
@@ -1359,15 +1369,30 @@ __global__ void __launch_bounds__(256, BatBound<MC>::min_blocks) bat_step(const 
     const int lane_g = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int64_t gpb = (int64_t)(blockDim.x / G);
-    const int64_t ngroups = gpb * gridDim.x;
     const int64_t g = *p.gen;
-    for (int64_t gid = (int64_t)blockIdx.x * gpb + threadIdx.x / G; gid < p.total; gid += ngroups) {
+    // Each block walks one contiguous range of the class's particles, so a
+    // group's consecutive particles are mostly of one instance: the class
+    // entry is found by one binary search and then advanced linearly.
+    const int64_t per_block = (p.total + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per_block;
+    const int64_t b1 = min(p.total, b0 + per_block);
+    int lo = -1;
+    int64_t ent_end = 0;
+    for (int64_t gid = b0 + threadIdx.x / G; gid < b1; gid += gpb) {
         // the class entry holding particle gid (first[] ascending)
-        int lo = 0, hi = p.n_ids - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(p.first + mid) <= gid) lo = mid;
-            else hi = mid - 1;
+        if (lo < 0 || gid >= ent_end) {
+            if (lo >= 0 && lo + 1 < p.n_ids && gid < __ldg(p.first + lo + 2)) {
+                ++lo;
+            } else {
+                int a = 0, z = p.n_ids - 1;
+                while (a < z) {
+                    const int mid = (a + z + 1) >> 1;
+                    if (__ldg(p.first + mid) <= gid) a = mid;
+                    else z = mid - 1;
+                }
+                lo = a;
+            }
+            ent_end = __ldg(p.first + lo + 1);
         }
         const int k = __ldg(p.ids + lo);
         const int64_t i = gid - __ldg(p.first + lo);
