@@ -154,7 +154,7 @@ struct StreamAcc<true> {
 };
 
 template <class Pos, bool F32R>
-__global__ void __launch_bounds__(256, 3) bat_stream(const BatParams p)
+__global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
 {
     using Val = typename std::conditional<F32R, float, double>::type;
     const int lane = threadIdx.x & 31;

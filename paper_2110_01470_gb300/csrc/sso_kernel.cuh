@@ -841,12 +841,15 @@ __device__ inline bool read_record(const uint64_t* rec, uint32_t tag, Winner& w,
 
 // Reads the records of ranks lane, lane+32, ... (up to four per pass, all
 // loads of a pass in flight together) and folds them into one candidate per
-// lane.  Returns false on timeout / abort.
-template <bool F32R>
+// lane.  Only a reader that sums the counters (COUNTS) loads the counter
+// words; the others read the four words that decide the winner, which keeps
+// the polled words of a pass in registers.  Returns false on timeout / abort.
+template <bool F32R, bool COUNTS>
 __device__ inline bool gather_records(const uint64_t* recs, int R, uint32_t tag, Cand& c,
                                       unsigned long long& acc, unsigned long long& rck,
                                       const KParams& p, const UnitDev& un)
 {
+    constexpr int NW = COUNTS ? REC_WORDS : RW_ACC;   // words read per record
     const int lane = threadIdx.x & 31;
     for (int k0 = 0; k0 * 32 < R; k0 += 4) {
         uint32_t pend = 0;
@@ -856,11 +859,21 @@ __device__ inline bool gather_records(const uint64_t* recs, int R, uint32_t tag,
         for (int64_t it = 0; pend; ++it) {
             uint64_t w[4][REC_WORDS];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (pend & (1u << q)) load_record(recs + (size_t)(lane + 32 * (k0 + q)) * REC_WORDS, w[q]);
+            for (int q = 0; q < 4; ++q) {
+                if (pend & (1u << q)) {
+                    const uint64_t* rp = recs + (size_t)(lane + 32 * (k0 + q)) * REC_WORDS;
+                    ldv2(rp + RW_IDX, w[q][0], w[q][1]);
+                    ldv2(rp + RW_V0, w[q][2], w[q][3]);
+                    if (COUNTS) ldv2(rp + RW_ACC, w[q][4], w[q][5]);
+                }
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if ((pend & (1u << q)) && record_ready(w[q], tag)) {
+                bool ready = (pend & (1u << q)) != 0;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) ready = ready && tagged(w[q][k], tag);
+                if (ready) {
+                    if (!COUNTS) { w[q][RW_ACC] = 0; w[q][RW_RCK] = 0; }
                     const Winner r = decode_record(w[q]);
                     Cand cq = cand_of<F32R>(r.idx, r.f64, r.lo, r.hi, r.has64, r.ver);
                     cq.rank = lane + 32 * (k0 + q);
@@ -896,7 +909,10 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
 
     Cand c = cand_none();
     unsigned long long acc = 0, rck = 0;
-    bool ok = gather_records<F32R>(recs, R, tag, c, acc, rck, p, un);
+    // only the block that writes the gBest record and log sums the counters
+    const bool counts = un.rank == 0 && finalize;
+    bool ok = counts ? gather_records<F32R, true>(recs, R, tag, c, acc, rck, p, un)
+                     : gather_records<F32R, false>(recs, R, tag, c, acc, rck, p, un);
     if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
     trace_point(gp + 1, 5);
     Cand win = cand_warp_reduce<F32R>(c, 1);
