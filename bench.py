@@ -214,6 +214,10 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 GEMM_TRAFFIC_BYTES = {(8192, 1000): 56.755712e6 + 1.514752e6}
+# DRAM bytes (read + write) of one 5000-generation launch of the persistent
+# kernel on shifted Rastrigin N=1024, D=100, FP32 + recheck, from one ncu
+# capture of this bench's launch (profiles/sso_generations_rastrigin_d100.md)
+GEN_TRAFFIC_BYTES = {("rastrigin", 1024, 100, 5000, "f32"): 1356032 + 38144}
 
 
 def measured_peaks():
@@ -484,8 +488,10 @@ def main():
     kernel_s = (sum(kern_ms) / len(kern_ms)) / 1e3
     peak = SM_COUNT * LANES_PER_SM * ALU_CLOCK_MHZ * 1e6 / 1e12     # T ops / s
     achieved = ops / kernel_s / 1e12
+    traffic = (GEN_TRAFFIC_BYTES.get((p0["fn"], p0["N"], p0["D"], t, prec))
+               if len(problems) == 1 else None)
     roofline = tensor or {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "sso_generations<float, true>" if prec == "f32" else
                           "sso_generations<..., false>",
                 "ops_per_update": ops / upd_per_step,
