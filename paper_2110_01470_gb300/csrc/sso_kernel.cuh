@@ -131,9 +131,11 @@ __device__ inline void give_up(const KParams& p, const UnitDev& un)
         p.status->where = un.inst * 65536 + un.rank;
     *(volatile int32_t*)&p.status->abort = 1;
 }
+// The abort flag is a global load: reading it on every poll would add a second
+// round trip to L2 after each poll's own loads, so it is read on every 32nd.
 __device__ __forceinline__ bool should_stop(const KParams& p, int64_t it)
 {
-    return it >= p.spin_limit || *(volatile int32_t*)&p.status->abort;
+    return it >= p.spin_limit || ((it & 31) == 31 && *(volatile int32_t*)&p.status->abort);
 }
 
 // ---------------------------------------------------------------------------
@@ -605,8 +607,11 @@ __device__ __forceinline__ Cand warp_fold(Cand best, int G, unsigned long long& 
                                           unsigned long long& n_rck)
 {
     if (G < 32) best = cand_warp_reduce<F32R>(best, G);
-    n_acc = warp_sum_u64(n_acc);
-    n_rck = warp_sum_u64(n_rck);
+    // only group leaders (lanes 0, G, 2G, ...) hold counts: lane 0 ends with the sum
+    for (int off = 16; off >= G; off >>= 1) {
+        n_acc += __shfl_xor_sync(0xffffffffu, n_acc, off);
+        n_rck += __shfl_xor_sync(0xffffffffu, n_rck, off);
+    }
     return best;
 }
 
@@ -731,14 +736,14 @@ __device__ __forceinline__ Winner step_c(const InstDev& in, const UnitDev& un, c
     trace_point(g, 6);
     int top = 1;
     while (2 * top < nw) top <<= 1;                 // lanes >= nw hold nothing
-    unsigned long long acc = lane < nw ? sh.warp_acc[lane] : 0ull;
-    unsigned long long rck = lane < nw ? sh.warp_rck[lane] : 0ull;
-    for (int off = top; off > 0; off >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        rck += __shfl_xor_sync(0xffffffffu, rck, off);
-    }
-    acc = __shfl_sync(0xffffffffu, acc, 0);
-    rck = __shfl_sync(0xffffffffu, rck, 0);
+    // The accepted and recheck counts travel as the halves of one word, so the
+    // reduction is one shuffle per level: the accepted count (at most one per
+    // particle, N < 2^31) never carries into the high half, which holds the
+    // recheck count (a statistic).
+    unsigned long long packed = lane < nw ? (sh.warp_acc[lane] | (sh.warp_rck[lane] << 32)) : 0ull;
+    for (int off = top; off > 0; off >>= 1) packed += __shfl_xor_sync(0xffffffffu, packed, off);
+    packed = __shfl_sync(0xffffffffu, packed, 0);
+    unsigned long long acc = packed & 0xffffffffull, rck = packed >> 32;
     trace_point(g, 7);
     Cand r = cand_warp_reduce<F32R>(c, 1, top);
     trace_point(g, 10);
@@ -916,8 +921,11 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
     if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
     trace_point(gp + 1, 5);
     Cand win = cand_warp_reduce<F32R>(c, 1);
-    acc = warp_sum_u64(acc);
-    rck = warp_sum_u64(rck);
+    if (counts) {               // halves of one word, as in step C
+        const unsigned long long packed = warp_sum_u64(acc | (rck << 32));
+        acc = packed & 0xffffffffull;
+        rck = packed >> 32;
+    }
     trace_point(gp + 1, 8);
 
     if (F32R && win.l2 <= win.mh) {
