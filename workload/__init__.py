@@ -20,6 +20,12 @@ measured on):
                  N ~ log-uniform int [64,4096], function uniform over
                  {sphere, Rastrigin, Rosenbrock, Ackley}, t=1000
   grad_d256      Rosenbrock and rotated Ackley, D=256, N=4096, t=3000
+  paper_rosenbrock_n{100,200,300,350}
+                 the paper's timing workload (Table 3.10): Rosenbrock, D=50,
+                 t=1000, bounds [-2.048, 2.048], no shift, FP64; the paper's
+                 interval triple Cw/Cp/Cg = 0.3/0.6/0.8 taken by probability
+                 as cumulative Cg/Cp/Cw = 0.2/0.5/0.8 (same branch
+                 probabilities: gBest 0.2, pBest 0.3, keep 0.3, fresh 0.2)
 """
 from __future__ import annotations
 
@@ -122,4 +128,9 @@ def config(name: str):
     if name == "grad_d256":
         ps = [problem(f, 4096, 256, seed=1, lattice="f32") for f in ("rosenbrock", "rot_ackley")]
         return dict(problems=ps, t=3000, precision="f32", polish=dict(K=50, steps=20, lr=1e-3))
+    if name.startswith("paper_rosenbrock_n"):
+        N = int(name[len("paper_rosenbrock_n"):])
+        p = problem("rosenbrock", N, 50, seed=1, lattice="f64", shift_range=(0.0, 0.0),
+                    Cg=0.2, Cp=0.5, Cw=0.8)
+        return dict(problems=[p], t=1000, precision="f64")
     raise KeyError(name)
