@@ -73,6 +73,7 @@ __device__ __forceinline__ int slot_of(int64_t g) { return (int)(g % SLOTS); }
 constexpr int BAR_VERDICT = 1;   // control warp -> compute warps: gBest of g-1 decided
 constexpr int BAR_CAND = 2;      // compute warps -> control warp: candidates of g written
 constexpr int BAR_PUB = 3;       // control warp -> compute warps: winner of g published
+constexpr int BAR_SPEC = 4;      // compute warps -> control warp: speculative candidates of g written
 __device__ __forceinline__ void bar_arrive(int id, int n)
 {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -297,6 +298,10 @@ __device__ __forceinline__ Cand cand_of(long long i, double f64, float lo, float
 struct BlockShared {
     Cand warp_cand[16];
     unsigned long long warp_acc[16], warp_rck[16];
+    // pipelined blocks: candidates posted before the verdict (speculative)
+    Cand spec_cand[16];
+    unsigned long long spec_acc[16];
+    int spec_bad[16];                     // 1: a decision of the warp needs FP64
     int flag;
     int row_changed;                      // step A replaced the gBest row in gs
     long long idx[MAX_UNITS_PER_BLOCK];   // identity (index, version) of the row in gs
@@ -772,6 +777,40 @@ __device__ __forceinline__ Winner step_c(const InstDev& in, const UnitDev& un, c
     return w;
 }
 
+// Step C of a pipelined block on the candidates its compute warps posted
+// before the verdict (valid when the gBest row did not change and no decision
+// needed FP64).  Returns false when the candidates' bounds overlap: the exact
+// fallback reads pBest state that the compute warps are still committing.
+template <bool F32R>
+__device__ __forceinline__ bool step_c_spec(const BlockShared& sh, Winner& w)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const Cand c = lane < nw ? sh.spec_cand[lane] : cand_none();
+    int top = 1;
+    while (2 * top < nw) top <<= 1;
+    unsigned long long acc = lane < nw ? sh.spec_acc[lane] : 0ull;
+    for (int off = top; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    const Cand r = cand_warp_reduce<F32R>(c, 1, top);
+    if (F32R && r.l2 <= r.mh) return false;
+    w.idx = r.i;
+    w.ver = r.ver;
+    w.acc = acc;
+    w.rck = 0;
+    if (!F32R) {
+        w.f64 = r.v;
+        w.has64 = 1;
+        w.lo = f64_to_f32_rd(r.v);
+        w.hi = f64_to_f32_ru(r.v);
+    } else {
+        w.has64 = r.has1;
+        w.f64 = r.has1 ? r.v : 0.0;
+        w.lo = r.l1;
+        w.hi = r.h1;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Records.
 __device__ inline void publish_record(uint64_t* rec, uint32_t tag, const Winner& w)
@@ -1022,7 +1061,7 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
 // Step D (warp 0) for a multi-block instance: publish the unit's winner row and record.
 template <class Pos>
 __device__ __forceinline__ void step_d_publish(const KParams& p, const InstDev& in, const UnitDev& un,
-                               const View<Pos>& v, const Winner& w, int64_t g)
+                               const View<Pos>& v, const Winner& w, int64_t g, bool with_record = true)
 {
     if (p.fault_skip_rank > 0 && un.inst == 0 && un.rank == p.fault_skip_rank - 1) return;
     constexpr int WPE = WordsPer<Pos>::value;
@@ -1036,7 +1075,17 @@ __device__ __forceinline__ void step_d_publish(const KParams& p, const InstDev& 
         ld4(src + 4 * ch, t);
         put_chunk(dst + (size_t)4 * ch * WPE, tag, t);
     }
-    if (lane == 0) publish_record(in.rec + ((size_t)slot_of(g) * R + un.rank) * REC_WORDS, tag, w);
+    if (lane == 0 && with_record) publish_record(in.rec + ((size_t)slot_of(g) * R + un.rank) * REC_WORDS, tag, w);
+}
+
+// The record alone (lane 0 of warp 0); its row follows with step_d_publish(..., false).
+// Readers poll the row words' tags, so a row published after its record is
+// only waited for, never read stale.
+__device__ __forceinline__ void publish_record_of(const KParams& p, const InstDev& in, const UnitDev& un,
+                                                  const Winner& w, int64_t g)
+{
+    if (p.fault_skip_rank > 0 && un.inst == 0 && un.rank == p.fault_skip_rank - 1) return;
+    publish_record(in.rec + ((size_t)slot_of(g) * in.R + un.rank) * REC_WORDS, (uint32_t)g, w);
 }
 
 // Step D (warp 0) for a whole-swarm unit: refresh the shared-memory gBest row.
@@ -1143,6 +1192,12 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nth = blockDim.x;
     if (warp == 0) {
+        if (lane == 0) {      // the control warp's own slots hold no candidate
+            sh.warp_cand[0] = cand_none(); sh.warp_acc[0] = 0; sh.warp_rck[0] = 0;
+            sh.spec_cand[0] = cand_none(); sh.spec_acc[0] = 0; sh.spec_bad[0] = 0;
+        }
+        __syncwarp();
+        const int nw = nth >> 5;
         for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
             trace_point(g, 0);
             if (g > 0) {
@@ -1154,13 +1209,26 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
             trace_point(g, 1);
             bar_arrive(BAR_VERDICT, nth);
             if (sh.flag) return;
-            bar_sync(BAR_CAND, nth);
+            // When the speculation held, the winner's record goes out on the
+            // candidates posted before the verdict, while the compute warps
+            // commit; the row follows once they have.
+            bar_sync(BAR_SPEC, nth);
             trace_point(g, 2);
-            if (lane == 0) { sh.warp_cand[0] = cand_none(); sh.warp_acc[0] = 0; sh.warp_rck[0] = 0; }
-            __syncwarp();
-            const Winner w = step_c<Pos, F32R>(desc, un, v, sh, g);
+            const bool bad = __any_sync(0xffffffffu, lane < nw && sh.spec_bad[lane] != 0);
+            Winner w;
+            bool sent = false;
+            if (!sh.row_changed && !bad) {
+                sent = step_c_spec<F32R>(sh, w);
+                if (sent && lane == 0) publish_record_of(p, desc, un, w, g);
+            }
             trace_point(g, 3);
-            step_d_publish<Pos>(p, desc, un, v, w, g);
+            bar_sync(BAR_CAND, nth);
+            if (sent) {
+                step_d_publish<Pos>(p, desc, un, v, w, g, false);
+            } else {
+                w = step_c<Pos, F32R>(desc, un, v, sh, g);
+                step_d_publish<Pos>(p, desc, un, v, w, g);
+            }
             trace_point(g, 4);
             if (g < p.g_end) bar_arrive(BAR_PUB, nth);
         }
@@ -1175,6 +1243,26 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
         if (g > p.g_begin) bar_sync(BAR_PUB, nth);
         PartState<Pos, MAXC> st;
         if (have) particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
+        {   // speculative candidate: exact unless the row changes or a decision needs FP64
+            unsigned long long s_acc = 0, s_rck = 0;
+            Cand sb = cand_none();
+            int bad = 0;
+            if (have && gr.lane_g == 0) {
+                if (F32R && st.undecided) bad = 1;
+                else {
+                    sb = particle_cand<Pos, F32R, MAXC>(i, st);
+                    s_acc = st.accept ? 1ull : 0ull;
+                }
+            }
+            bad = __any_sync(0xffffffffu, bad);
+            sb = warp_fold<F32R>(sb, in.G, s_acc, s_rck);
+            if (lane == 0) {
+                sh.spec_cand[warp] = sb;
+                sh.spec_acc[warp] = s_acc;
+                sh.spec_bad[warp] = bad;
+            }
+        }
+        bar_arrive(BAR_SPEC, nth);
         if (threadIdx.x == 32) trace_point(g, 7);
         bar_sync(BAR_VERDICT, nth);
         if (sh.flag) return;
