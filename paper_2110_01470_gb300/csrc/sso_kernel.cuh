@@ -661,7 +661,9 @@ __device__ inline void write_gbest(const InstDev& in, const Winner& w, int64_t g
     gb->gen = g;
     gb->accepted = (int64_t)w.acc;
     gb->rechecks = (int64_t)w.rck;
-    gb->total_rechecks += (int64_t)w.rck;
+    // a reduction without a return value: no load round trip on the path of
+    // every generation (and none at all when there was no recheck)
+    if (w.rck) atomicAdd(reinterpret_cast<unsigned long long*>(&gb->total_rechecks), (unsigned long long)w.rck);
     gb->f64 = w.f64;
     gb->lo = w.lo;
     gb->hi = w.hi;
