@@ -214,10 +214,11 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 GEMM_TRAFFIC_BYTES = {(8192, 1000): 56.755712e6 + 1.514752e6}
-# DRAM bytes (read + write) of one 5000-generation launch of the persistent
-# kernel on shifted Rastrigin N=1024, D=100, FP32 + recheck, from one ncu
-# capture of this bench's launch (profiles/sso_generations_rastrigin_d100.md)
-GEN_TRAFFIC_BYTES = {("rastrigin", 1024, 100, 5000, "f32"): 1826816 + 33536}
+# DRAM bytes (read + write) of one launch of the persistent kernel, from an
+# ncu capture of the kernel as it stands, keyed by (fn, N, D, t, precision).
+# Empty: the last capture (profiles/sso_generations_rastrigin_d100.md, 1.86 MB
+# per 5000-generation launch) predates the current revision of the kernel.
+GEN_TRAFFIC_BYTES = {}
 
 
 def measured_peaks():

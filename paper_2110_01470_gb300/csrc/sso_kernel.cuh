@@ -304,6 +304,8 @@ struct BlockShared {
     int spec_bad[16];                     // 1: a decision of the warp needs FP64
     int flag;
     int row_changed;                      // step A replaced the gBest row in gs
+    unsigned long long lag_r2;            // pipelined rank 0: second-round FP64 evaluations of
+                                          // the generation whose counters are still to be logged
     long long idx[MAX_UNITS_PER_BLOCK];   // identity (index, version) of the row in gs
     uint32_t ver[MAX_UNITS_PER_BLOCK];
 };
@@ -940,12 +942,58 @@ __device__ inline bool gather_records(const uint64_t* recs, int R, uint32_t tag,
     return true;
 }
 
+// Pipelined rank 0 (one warp): the accepted / recheck counters of generation
+// gq from every block's record, written into gq's log entry and the running
+// recheck total.  Run by a compute warp after its commit of gq+1 (or by the
+// control warp in the epilogue), when the counter words are present, so the
+// control warp of the block that keeps the gBest state never waits for them.
+// Returns false on timeout (after give_up).
+static __device__ __noinline__ bool fill_counts(const KParams& p, const InstDev& in, const UnitDev& un, int64_t gq,
+                                         unsigned long long extra_rck)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t tag = (uint32_t)gq;
+    const uint64_t* recs = in.rec + (size_t)slot_of(gq) * in.R * REC_WORDS;
+    unsigned long long packed = 0;
+    bool ok = true;
+    for (int r = lane; r < in.R && ok; r += 32) {
+        for (int64_t it = 0;; ++it) {
+            uint64_t a, b;
+            ldv2(recs + (size_t)r * REC_WORDS + RW_ACC, a, b);
+            if (tagged(a, tag) && tagged(b, tag)) {
+                packed += (a & 0xffffffffull) | ((b & 0xffffffffull) << 32);
+                break;
+            }
+            if (should_stop(p, it)) { give_up(p, un); ok = false; break; }
+            if (it > 16) __nanosleep(20);
+        }
+    }
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    packed = warp_sum_u64(packed);
+    if (lane == 0) {
+        const unsigned long long acc = packed & 0xffffffffull, rck = (packed >> 32) + extra_rck;
+        if (in.log_stride > 0 && in.log_cap > 0 && (gq % in.log_stride) == 0) {
+            LogDev* e = in.log + ((gq / in.log_stride) % in.log_cap);
+            e->accepted = (int64_t)acc;
+            e->rechecks = (int64_t)rck;
+        }
+        if (rck) atomicAdd(reinterpret_cast<unsigned long long*>(&in.gb->total_rechecks), rck);
+    }
+    __syncwarp();
+    return true;
+}
+
 // Step A (warp 0) for a unit of a multi-block instance: decide the gBest of
 // generation gp from the records and make sure shared memory holds its row.
+// With `lag` (pipelined blocks), rank 0 writes gp's gBest state and log entry
+// without the counters, which a compute warp of that block fills in during
+// the next generation (fill_counts; the last generation's in the epilogue):
+// the winner's keys alone are on the critical path of the block that keeps
+// the gBest state, which every other block waits for.
 // Sets sh.flag when the launch is aborting.
 template <class Pos, bool F32R>
 __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const UnitDev& un, const View<Pos>& v,
-                       int uslot, Pos* gs, int64_t gp, bool finalize, BlockShared& sh)
+                       int uslot, Pos* gs, int64_t gp, bool finalize, BlockShared& sh, bool lag = false)
 {
     const int lane = threadIdx.x & 31;
     const int R = in.R;
@@ -956,7 +1004,8 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
     Cand c = cand_none();
     unsigned long long acc = 0, rck = 0;
     // only the block that writes the gBest record and log sums the counters
-    const bool counts = un.rank == 0 && finalize;
+    // (and, lagging, not yet)
+    const bool counts = un.rank == 0 && finalize && !lag;
     bool ok = counts ? gather_records<F32R, true>(recs, R, tag, c, acc, rck, p, un)
                      : gather_records<F32R, false>(recs, R, tag, c, acc, rck, p, un);
     if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
@@ -1010,7 +1059,11 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
         win.has1 = 1;
         win.l1 = f64_to_f32_rd(win.v);
         win.h1 = f64_to_f32_ru(win.v);
-        rck += warp_sum_u64(r2);
+        r2 = warp_sum_u64(r2);
+        rck += r2;
+        if (lag && lane == 0) sh.lag_r2 = r2;
+    } else if (lag && lane == 0) {
+        sh.lag_r2 = 0;
     }
 
     // Fetch the winner's row if it is not the one already in shared memory.
@@ -1044,8 +1097,8 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
             Winner w;
             w.idx = win.i;
             w.ver = win.ver;
-            w.acc = acc;
-            w.rck = rck;
+            w.acc = lag ? 0 : acc;       // lagging: fill_counts writes them
+            w.rck = lag ? 0 : rck;
             w.has64 = F32R ? win.has1 : 1;
             w.f64 = F32R ? (win.has1 ? win.v : 0.0) : win.v;
             w.lo = F32R ? win.l1 : f64_to_f32_rd(win.v);
@@ -1203,7 +1256,7 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
         for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
             trace_point(g, 0);
             if (g > 0) {
-                step_a<Pos, F32R>(p, desc, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh);
+                step_a<Pos, F32R>(p, desc, un, v, slot, gs, g - 1, g - 1 >= p.g_begin, sh, F32R);
             } else if (lane == 0) {
                 sh.row_changed = 0;
             }
@@ -1268,6 +1321,7 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
         if (threadIdx.x == 32) trace_point(g, 7);
         bar_sync(BAR_VERDICT, nth);
         if (sh.flag) return;
+        const unsigned long long r2_prev = sh.lag_r2;   // stashed by step A of g-1
         if (have && sh.row_changed)       // the gBest moved: recompute with the new row
             particle_compute<Pos, F32R, MAXC>(in, v, gs, i, e, g, gr.lane_g, gr.gmask, st);
         unsigned long long n_acc = 0, n_rck = 0;
@@ -1284,6 +1338,11 @@ __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const Unit
         }
         if (threadIdx.x == 32) trace_point(g, 6);
         bar_arrive(BAR_CAND, nth);
+        // rank 0: the counters of g-1 go into its log entry while this warp
+        // would otherwise wait for the publication
+        // (FP32 fitness only: with FP64 fitness the compute warps have no slack
+        // before the next speculative candidates, and the counters stay in step A)
+        if (F32R && un.rank == 0 && warp == 1 && g - 1 >= p.g_begin) fill_counts(p, desc, un, g - 1, r2_prev);
     }
 }
 
@@ -1392,7 +1451,13 @@ __global__ void __launch_bounds__(GenBound<MC>::threads) sso_generations(const K
         const View<Pos> v = make_view<Pos>(in, un, smem);
         if (in.R > 1 && warp == 0) {
             Pos* gs = reinterpret_cast<Pos*>(smem + un.smem_off);
-            step_a<Pos, F32R>(p, in, un, v, u - u0, gs, p.g_end, true, sh);
+            // pipelined blocks lag their counters by one generation: the last
+            // one is logged here, after step A of the last generation
+            const bool lag = F32R && un.pipelined != 0;
+            step_a<Pos, F32R>(p, in, un, v, u - u0, gs, p.g_end, true, sh, lag);
+            __syncwarp();
+            if (lag && un.rank == 0 && !sh.flag && !fill_counts(p, in, un, p.g_end, sh.lag_r2) && lane == 0)
+                sh.flag = 1;
         }
         __syncthreads();
         if (sh.flag) return;
