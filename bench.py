@@ -20,7 +20,7 @@ the FP64-fitness path on the same workload is timed beside it.
 
 Multi-GPU: replicas only (one independent swarm per rank, stream id = rank,
 no collective on the data path); value = all ranks' updates / max time.
-`--impl reference` times the CPU oracle (the reference arm of this build).
+`--impl reference` times the CPU oracle on the host cores (the reference arm).
 """
 from __future__ import annotations
 

@@ -59,7 +59,7 @@ typedef enum {
                                  is left in an undefined state and must be destroyed
                                  or reloaded with psso_load                          */
     PSSO_ERR_STATE = 5,       /* call not valid in the handle's current state       */
-    PSSO_ERR_UNSUPPORTED = 6  /* valid request this build does not implement        */
+    PSSO_ERR_UNSUPPORTED = 6  /* valid request the library does not implement       */
 } psso_status;
 
 /* Test functions (Table 3.2 of the paper; shifted by o, rotated by M).

@@ -399,7 +399,7 @@ int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
     return 0;
 }
 
-/* Maximum OpenMP threads this build can use (1 without OpenMP). */
+/* Maximum OpenMP threads the compiled oracle can use (1 without OpenMP). */
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

@@ -156,7 +156,7 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
         return PSSO_ERR_ARG;
     }
     if (fn >= PSSO_ROT_ELLIPSOID) {
-        set_last_error("psso_evaluate_noalloc: rotated functions are not available in this build");
+        set_last_error("psso_evaluate_noalloc: rotated functions are not available through this entry point");
         return PSSO_ERR_UNSUPPORTED;
     }
     if (fn == PSSO_ELLIPSOID && !weights) {

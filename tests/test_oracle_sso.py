@@ -155,3 +155,22 @@ def test_bruteforce_grid(fn, D):
     assert best >= gmin - lip * h * np.sqrt(D) / 2 - 1e-12
     assert best >= 0.0                                          # the true minimum is 0 at o
     assert best <= gmin + 0.05 * max(1.0, gmin) + 0.05
+
+
+def test_paper_triple_mapping_keeps_branch_probabilities():
+    """Reading of Eq. 2.1's interval order: the paper's Cw < Cp < Cg triple
+    (0.3, 0.6, 0.8; keep x on [0, Cw), pBest on [Cw, Cp), gBest on [Cp, Cg),
+    fresh on [Cg, 1)) is run as cumulative gBest / pBest / keep thresholds with
+    the same branch probabilities.  The paper's widths are computed here from
+    its own order; the oracle's branch counts on the paper workload must match
+    them within 5 sigma."""
+    import workload
+    cw, cp, cg = 0.3, 0.6, 0.8
+    paper = {"keep": cw, "pbest": cp - cw, "gbest": cg - cp, "fresh": 1.0 - cg}
+    p = workload.config("paper_rosenbrock_n100")["problems"][0]
+    r = oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"], p["seed"], 20,
+                   o=p["o"])
+    n = r["branch"].sum()
+    got = dict(zip(["gbest", "pbest", "keep", "fresh"], r["branch"] / n))
+    for k, want in paper.items():
+        assert abs(got[k] - want) <= 5 * np.sqrt(want * (1 - want) / n), (k, got[k], want)
