@@ -213,6 +213,31 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Replicas on N GPUs: every rank runs the same workload on its own Philox
+# streams (no collective on the data path); only the step time is reduced.
+def replica_problems(problems, rank):
+    """The workload's problems for one rank: instance k of rank r draws from
+    Philox stream k + r * count, so no two instances of the job share draws."""
+    count = len(problems)
+    return [dict(p, sid=int(p["sid"]) + rank * count) for p in problems]
+
+
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step, steps, world, max_total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return units_per_step * steps * world / (max_total_ms / 1e3)
+
+
 GEMM_TRAFFIC_BYTES = {(8192, 1000): 56.755712e6 + 1.514752e6}
 # DRAM bytes (read + write) of one launch of the persistent kernel, from an
 # ncu capture of the kernel as it stands, keyed by (fn, N, D, t, precision).
@@ -379,7 +404,7 @@ def main():
 
     cfg = workload.config(args.workload)
     t = args.generations or cfg["t"]
-    problems = [dict(p, sid=rank) for p in cfg["problems"]]
+    problems = replica_problems(cfg["problems"], rank)
     prec = cfg["precision"]
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -435,12 +460,9 @@ def main():
     best = psso.psso_best(h, 0)
     psso.psso_destroy(h)
     total = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
-    value = upd_per_step * args.steps * world / (total / 1e3)
-    evals = evals_per_step * args.steps * world / (total / 1e3)
+    total = max_over_ranks(total, dist, "cuda")
+    value = job_rate(upd_per_step, args.steps, world, total)
+    evals = job_rate(evals_per_step, args.steps, world, total)
 
     # --- FP64-fitness arm on the same workload ------------------------------------------
     fp64 = None
