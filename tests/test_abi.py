@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a and exports every entry point that
 include/psso.h declares (no GPU needed: nothing is called)."""
+import ctypes
 import os
 import re
 import shutil
@@ -63,3 +64,31 @@ def test_product_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "psso_oracle" not in text and "liboracle" not in text, f
+
+
+def test_binding_structs_match_header(tmp_path):
+    """Every struct of the ABI has the same size and field offsets in the C
+    header (compiled by gcc) and in the ctypes binding."""
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    import paper_2110_01470_gb300 as psso
+    structs = {"psso_problem": psso.psso_problem, "psso_config": psso.psso_config,
+               "psso_log_entry": psso.psso_log_entry, "psso_stats_t": psso.psso_stats_t,
+               "psso_tune_report": psso.psso_tune_report}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "psso.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {tuple(l.split()[:2]): int(l.split()[2]) for l in got if l.strip()}
+    for name, cls in structs.items():
+        assert c[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert c[(name, field)] == getattr(cls, field).offset, (name, field)
