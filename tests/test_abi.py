@@ -92,3 +92,13 @@ def test_binding_structs_match_header(tmp_path):
         assert c[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert c[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_binding_config_fields():
+    """The binding builds a psso_config from field names and rejects unknown ones."""
+    import paper_2110_01470_gb300 as psso
+    cfg = psso._config("f32", {"batch_blocks_per_sm": 3, "threads_per_block": 384, "log_stride": 1})
+    assert (cfg.precision, cfg.batch_blocks_per_sm, cfg.threads_per_block, cfg.log_stride) == (1, 3, 384, 1)
+    assert cfg.reserved == 0 and cfg.stream is None
+    with pytest.raises(TypeError):
+        psso._config("f64", {"threads": 64})
