@@ -1238,8 +1238,14 @@ __device__ Cand unit_spec(const KParams& p, const InstDev& in, const UnitDev& un
 // the verdict of step A says the row was current, their results are committed
 // as computed; otherwise they are recomputed.  The compute warps start only
 // after the publication so that steps C and D, on the critical path of every
-// block, do not share issue slots with them.  Three named barriers carry the
-// hand-offs.
+// block, do not share issue slots with them.  Before the verdict they post
+// the arg-min candidates their evaluation implies: when the row did not change
+// and no decision needs FP64, the control warp sends the record on those while
+// the compute warps commit, and the row after the commit.  In rank 0 (FP32
+// fitness) a compute warp also fills in the previous generation's counters of
+// the gBest log.  Four named barriers carry the hand-offs: speculative
+// candidates and committed candidates (compute -> control), verdict and
+// publication (control -> compute).
 template <class Pos, bool F32R, int MAXC>
 __device__ void pipelined_unit(const KParams& p, const InstDev& desc, const UnitDev& un,
                                const View<Pos>& v, Pos* gs, int slot, BlockShared& sh)
