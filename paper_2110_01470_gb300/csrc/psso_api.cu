@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "psso.h"
 #include "psso_internal.h"
 #include "rot_pipeline.h"
@@ -15,6 +17,15 @@
 using namespace psso;
 
 namespace {
+
+// NVTX range around an entry point, so that a profiler's timeline shows the
+// host side of create / run / reset / sync / best (no effect without one).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 thread_local std::string g_last_error;
 
@@ -664,6 +675,7 @@ const char* psso_last_error(void) { return g_last_error.c_str(); }
 psso_status psso_create_ex(const psso_problem* problems, int32_t count, const psso_config* cfg,
                            psso_handle* out)
 {
+    const Range range("psso_create_ex");
     if (!out) return fail(PSSO_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!problems || count < 1 || count > 65536) return fail(PSSO_ERR_ARG, "need 1..65536 problems");
@@ -874,6 +886,7 @@ psso_status psso_create(psso_fn fn, int64_t N, int64_t D, double lb, double ub, 
 
 psso_status psso_run(psso_handle h, int64_t generations)
 {
+    const Range range("psso_run");
     if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
     if (generations < 0) return fail(PSSO_ERR_ARG, "generations must be >= 0");
     if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier; destroy it or psso_load a state");
@@ -892,6 +905,7 @@ psso_status psso_run(psso_handle h, int64_t generations)
 
 psso_status psso_reset(psso_handle h)
 {
+    const Range range("psso_reset");
     if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
     CUDA_TRY(cudaSetDevice(h->device));
     const size_t logcap = h->cfg.log_stride > 0 ? (size_t)h->cfg.log_capacity : 0;
@@ -917,6 +931,7 @@ psso_status psso_reset(psso_handle h)
 
 psso_status psso_sync(psso_handle h)
 {
+    const Range range("psso_sync");
     if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
     return read_status(h);
 }
@@ -939,6 +954,7 @@ static psso_status copy_row(psso_ctx* h, const HostInst& I, size_t off, int64_t 
 
 psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* index, double* row)
 {
+    const Range range("psso_best");
     if (!h) return fail(PSSO_ERR_ARG, "handle is NULL");
     if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
     psso_status st = read_status(h);

@@ -102,3 +102,22 @@ def test_binding_config_fields():
     assert cfg.reserved == 0 and cfg.stream is None
     with pytest.raises(TypeError):
         psso._config("f64", {"threads": 64})
+
+
+def test_entry_points_fail_cleanly_without_gpu(libpath):
+    """Without a GPU, the entry points return an error status (no crash, no
+    CPU fallback); the NVTX ranges around them are inert."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the GPU tests cover the entry points")
+    import paper_2110_01470_gb300 as psso
+    import workload
+    psso.load(libpath)
+    p = workload.problem("sphere", 16, 4, seed=1)
+    with pytest.raises(psso.PssoError) as e:
+        psso.psso_create_ex([p], "f64")
+    assert e.value.status == psso.PSSO_ERR_CUDA
+    with pytest.raises(psso.PssoError):
+        psso.psso_run(None, 1)
+    with pytest.raises(psso.PssoError):
+        psso.psso_autotune([p], "f64", generations=1)
