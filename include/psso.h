@@ -27,7 +27,9 @@
  *   * Eq. 2.1 with cumulative thresholds Cg <= Cp <= Cw in [0,1]: a 32-bit
  *     Philox-4x32-10 word r per variable picks gBest_j if r < T(Cg), pBest_ij if
  *     r < T(Cp), keeps x_ij if r < T(Cw), else a fresh uniform value in [lb,ub],
- *     with T(C) = round-half-even(C * 2^32).
+ *     with T(C) = round-half-even(C * 2^32).  psso_problem.order selects the
+ *     interval order of Eq. 2.1 as printed instead (x, pBest, gBest, fresh with
+ *     Cw <= Cp <= Cg).
  *   * Draws are keyed by (seed, stream_id) with counter (variable block,
  *     particle, generation, tag); the result of a run depends on nothing else
  *     (not on the launch shape, the GPU, or how generations are split between
@@ -99,6 +101,16 @@ typedef enum { PSSO_LATTICE_F64 = 0, PSSO_LATTICE_F32 = 1 } psso_lattice;
  *                lattice and a float-exact shift. */
 typedef enum { PSSO_PREC_F64 = 0, PSSO_PREC_F32_RECHECK = 1 } psso_precision;
 
+/* Interval order of Eq. 2.1 (psso_problem.order).
+ *   GPX    r < T(Cg) -> gBest_j, r < T(Cp) -> pBest_ij, r < T(Cw) -> x_ij, else a
+ *          fresh value; needs 0 <= Cg <= Cp <= Cw <= 1 (the default).
+ *   PAPER  the order Eq. 2.1 prints: r < T(Cw) -> x_ij, r < T(Cp) -> pBest_ij,
+ *          r < T(Cg) -> gBest_j, else a fresh value; needs 0 <= Cw <= Cp <= Cg
+ *          <= 1 (e.g. the paper's Cw, Cp, Cg = 0.3, 0.6, 0.8, Sec. 3.4).
+ * Both draw the same words r; for the same branch probabilities they give
+ * different, equally distributed trajectories. */
+typedef enum { PSSO_ORDER_GPX = 0, PSSO_ORDER_PAPER = 1 } psso_order;
+
 /* One problem instance (one independent swarm). */
 typedef struct {
     int32_t fn;          /* psso_fn                                                */
@@ -106,10 +118,10 @@ typedef struct {
     int64_t N;           /* particles, 1 .. 2^31-1                                  */
     int64_t D;           /* variables, 1 .. 1024                                    */
     double lb, ub;       /* search bounds, lb < ub, finite                          */
-    double Cg, Cp, Cw;   /* cumulative Eq. 2.1 thresholds, 0 <= Cg <= Cp <= Cw <= 1 */
+    double Cg, Cp, Cw;   /* cumulative Eq. 2.1 thresholds, ordered as `order` says  */
     uint64_t seed;       /* Philox key                                              */
     uint32_t stream_id;  /* Philox counter stream, < 2^24 (independent instances)   */
-    uint32_t reserved;   /* must be 0                                               */
+    uint32_t order;      /* psso_order (0 = GPX)                                    */
     const double* shift;    /* host, D values, or NULL for o = 0                    */
     const double* weights;  /* host, D values; required by the ellipsoid functions  */
     const double* rotation; /* host, D*D row-major M; required by rotated functions */
@@ -218,7 +230,9 @@ psso_status psso_sync(psso_handle h);
 
 /* gBest of instance `instance` after the last completed generation: FP64
  * fitness (`value`), particle index, and the D-value row (`row`, may be NULL).
- * In F32_RECHECK mode the FP64 value is computed on demand.  Synchronises. */
+ * In F32_RECHECK mode the FP64 value is computed on demand.  Synchronises.
+ * Paper: Alg. 2's final step, which sends the data back to the CPU to
+ * calculate fOpt (the best fitness found; Table 3.1's GBest and fOpt). */
 psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* index,
                       double* row);
 
@@ -273,15 +287,21 @@ psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const double* X, con
  * and the outputs f (N doubles) and err (N doubles, or NULL).  It allocates
  * nothing: its only scratch, the padded shift / weight vectors, lives in one
  * static device array of 24 KiB (D at most 1024; larger D is rejected with
- * PSSO_ERR_ARG).  With PSSO_PREC_F32_RECHECK every X value must be a float;
- * rows holding other values get NaN in f and err.
+ * PSSO_ERR_ARG; N at most 8 * (2^31 - 1)).  With PSSO_PREC_F32_RECHECK the
+ * FP32 terms and the bound err are only valid for float inputs: every row
+ * holding an X value that is not a float gets NaN in f and err, and so does
+ * every row when a shift value is not a float.  Rotated functions are not
+ * available here (they need a D x D matrix, which does not fit the static
+ * scratch): they return PSSO_ERR_UNSUPPORTED.
  *
  * Work is enqueued on `stream` (cudaStream_t, NULL = default) and the call
  * returns without waiting.  The first call on a device looks up the scratch
  * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  Every call shares the array and
- * rewrites what it reads, so calls that overlap on the GPU (unordered streams)
- * race on it. */
+ * that first call before any stream capture.  The address is cached for the
+ * life of the process, so the library must not be used on a device across a
+ * cudaDeviceReset.  Every call shares the array and rewrites what it reads
+ * (calls queued one after another on one stream are safe); calls that overlap
+ * on the GPU (unordered streams) race on it. */
 psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, const double* X,
                                   const double* shift, const double* weights, int32_t precision,
                                   double* f, double* err, void* stream);

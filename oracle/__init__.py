@@ -91,6 +91,9 @@ def _load():
     lib.oracle_run.argtypes = [i32, i32, i64, i64, d, d, d, d, d, u64, u32, vp, vp, vp,
                                i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.oracle_run.restype = i32
+    lib.oracle_run_ex.argtypes = [i32, i32, i32, i32, i64, i64, d, d, d, d, d, u64, u32, vp, vp,
+                                  vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.oracle_run_ex.restype = i32
     lib.oracle_max_threads.argtypes = []
     lib.oracle_max_threads.restype = i32
     _lib = lib
@@ -147,10 +150,17 @@ def fitness(fn, x, o=None, w=None, M=None):
     return float(lib.oracle_fitness(FN[fn], D, _ptr(x), _ptr(o), _ptr(w), _ptr(M)))
 
 
+ORDER = {"gpx": 0, "paper": 1}
+FLOW = {"sync": 0, "async": 1}
+
+
 def run(fn, N, D, lb, ub, Cg, Cp, Cw, seed, t, *, lattice="f64", sid=0, o=None, w=None,
-        M=None, nthreads=1):
+        M=None, nthreads=1, order="gpx", flow="sync"):
     """One SSO run of ``t`` generations.  Returns a dict of numpy arrays:
-    X, P (N x D), pF (N), G (D), log_b, log_v, log_acc (t+1), branch (4)."""
+    X, P (N x D), pF (N), G (D), log_b, log_v, log_acc (t+1), branch (4).
+    ``order``: "gpx" (intervals gBest, pBest, keep; Cg <= Cp <= Cw) or "paper"
+    (Eq. 2.1 as printed: keep, pBest, gBest; Cw <= Cp <= Cg).  ``flow``: "sync"
+    (Alg. 2-4) or "async" (Alg. 1, particle by particle)."""
     lib = _load()
     o = _f64(o, D)
     w = _f64(w, D)
@@ -163,13 +173,23 @@ def run(fn, N, D, lb, ub, Cg, Cp, Cw, seed, t, *, lattice="f64", sid=0, o=None, 
     log_v = np.empty(t + 1, dtype=np.float64)
     log_acc = np.empty(t + 1, dtype=np.int64)
     branch = np.zeros(4, dtype=np.int64)
-    rc = lib.oracle_run(FN[fn], LATTICE[lattice], N, D, lb, ub, Cg, Cp, Cw, seed, sid,
-                        _ptr(o), _ptr(w), _ptr(M), t, nthreads, _ptr(X), _ptr(P), _ptr(pF),
-                        _ptr(G), _ptr(log_b), _ptr(log_v), _ptr(log_acc), _ptr(branch))
+    rc = lib.oracle_run_ex(FN[fn], LATTICE[lattice], ORDER[order], FLOW[flow], N, D, lb, ub,
+                           Cg, Cp, Cw, seed, sid, _ptr(o), _ptr(w), _ptr(M), t, nthreads,
+                           _ptr(X), _ptr(P), _ptr(pF), _ptr(G), _ptr(log_b), _ptr(log_v),
+                           _ptr(log_acc), _ptr(branch))
     if rc != 0:
         raise ValueError(f"oracle_run rejected its arguments (code {rc})")
     return dict(X=X, P=P, pF=pF, G=G, log_b=log_b, log_v=log_v, log_acc=log_acc,
                 branch=branch)
+
+
+def run_problem(p, t, *, nthreads=1, flow="sync"):
+    """``run`` on a problem description (a dict with the keys fn, N, D, lb, ub,
+    Cg, Cp, Cw, seed and optional lattice, sid, order, o, w, M)."""
+    return run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"], p["seed"],
+               t, lattice=p.get("lattice", "f64"), sid=p.get("sid", 0), o=p.get("o"),
+               w=p.get("w"), M=p.get("M"), nthreads=nthreads, order=p.get("order", "gpx"),
+               flow=flow)
 
 
 def max_threads():

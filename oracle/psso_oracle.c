@@ -25,11 +25,17 @@
  *                  Sec. 2.3.2); pBest update with "<=" (Alg. 3); gBest = the
  *                  lowest-index arg-min of pF (Alg. 4, with a deterministic
  *                  tie-break).
+ *   oracle_run_ex adds the asynchronous flow of Alg. 1 (the sequential CPU-SSO:
+ *   particle by particle, gBest replaced as soon as a particle beats it) and
+ *   the interval order Eq. 2.1 prints.
  *
  * Readings of the paper taken here (the paper is silent or garbled on each):
- *   * Eq. 2.1's intervals are taken in the order gBest, pBest, keep, fresh with
- *     cumulative thresholds Cg <= Cp <= Cw (the same four-way split as Eq. 2.1,
- *     which lists them as keep, pBest, gBest, fresh).
+ *   * Eq. 2.1's intervals are taken by default in the order gBest, pBest, keep,
+ *     fresh with cumulative thresholds Cg <= Cp <= Cw (the same four-way split
+ *     as Eq. 2.1, which lists them as keep, pBest, gBest, fresh with
+ *     Cw <= Cp <= Cg; order 1 of oracle_run_ex takes that printed order).
+ *   * Alg. 1's second test is printed as a repeat of the first ("solF < pF");
+ *     it is read as the gBest test solF < gF.
  *   * The uniform draw rho is a 32-bit Philox word r; "rho < C" is the integer
  *     test r < T with T = round-half-even(C * 2^32).
  *   * Random numbers are Philox-4x32-10 blocks (Salmon, Moraes, Dror, Shaw,
@@ -313,7 +319,46 @@ double oracle_fitness(int fn, int64_t D, const double* x, const double* o,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Eq. 2.1 for one particle: every variable of x_i is replaced by gBest_j,
+ * pBest_ij, kept, or drawn fresh, according to the interval its draw falls in.
+ *   order 0: intervals [0, Cg) -> gBest, [Cg, Cp) -> pBest, [Cp, Cw) -> keep,
+ *            [Cw, 1) -> fresh (cumulative Cg <= Cp <= Cw);
+ *   order 1: the order Eq. 2.1 prints: [0, Cw) -> keep, [Cw, Cp) -> pBest,
+ *            [Cp, Cg) -> gBest, [Cg, 1) -> fresh (cumulative Cw <= Cp <= Cg).
+ * T1 <= T2 <= T3 are the interval ends on the 32-bit draw.  nb counts the
+ * branches taken (gBest, pBest, keep, fresh). */
+enum { BR_GBEST = 0, BR_PBEST = 1, BR_KEEP = 2, BR_FRESH = 3 };
+
+static void stepwise_update(int order, int lattice, uint64_t seed, uint32_t sid, uint32_t g,
+                            uint32_t i, int64_t D, double lb, double ub, uint64_t T1,
+                            uint64_t T2, uint64_t T3, const double* G, const double* p,
+                            double* x, int64_t nb[4])
+{
+    const int first = order ? BR_KEEP : BR_GBEST;
+    const int third = order ? BR_GBEST : BR_KEEP;
+    for (int64_t j = 0; j < D; ++j) {
+        uint64_t r = oracle_rho(seed, sid, g, i, (uint32_t)j);
+        int br = (r < T1) ? first : (r < T2) ? BR_PBEST : (r < T3) ? third : BR_FRESH;
+        if (br == BR_GBEST) x[j] = G[j];
+        else if (br == BR_PBEST) x[j] = p[j];
+        else if (br == BR_FRESH)
+            x[j] = oracle_fresh(lattice, seed, sid, TAG_FRESH, g, i, (uint32_t)j, lb, ub);
+        nb[br]++;
+    }
+}
+
 /* One SSO run.  Returns 0, or a negative code for invalid arguments.
+ *   order : 0 or 1, the interval order of Eq. 2.1 (see stepwise_update).
+ *   flow  : 0 = synchronous generations (Alg. 2, the PSSO flow): every
+ *           particle searches with the gBest of the previous generation, pBest
+ *           is replaced when f <= pF (Alg. 3), and gBest is then the
+ *           lowest-index arg-min of pF (Alg. 4);
+ *           1 = asynchronous generations (Alg. 1, the sequential CPU-SSO):
+ *           particles are taken one after the other in index order, each
+ *           searches (Eq. 2.1), is evaluated, replaces its pBest when f < pF
+ *           and the gBest when f < gF (both strict, as Alg. 1 writes them), so
+ *           particle i already sees a gBest found earlier in the same
+ *           generation.  Generation 0 is the same in both flows.
  *   X, P : N*D row-major (outputs: final positions and pBests)
  *   pF   : N (output: final pBest fitness)
  *   G    : D (output: final gBest row)
@@ -321,18 +366,22 @@ double oracle_fitness(int fn, int64_t D, const double* x, const double* o,
  *          gBest index, its fitness and the number of accepted pBest updates.
  *   branch : 4 counters or NULL -- how often each branch of Eq. 2.1 fired
  *          (gBest, pBest, keep, fresh) over generations 1..t.
- *   nthreads : >1 parallelises the per-particle work of a generation with
- *          OpenMP; every particle's work is independent and the arg-min is
- *          sequential, so the result is bit-identical to nthreads = 1. */
-int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
-               double Cg, double Cp, double Cw, uint64_t seed, uint32_t sid,
-               const double* o, const double* w, const double* M,
-               int64_t t, int nthreads,
-               double* X, double* P, double* pF, double* G,
-               int64_t* log_b, double* log_v, int64_t* log_acc, int64_t* branch)
+ *   nthreads : >1 parallelises the per-particle work of a synchronous
+ *          generation with OpenMP; every particle's work is independent and
+ *          the arg-min is sequential, so the result is bit-identical to
+ *          nthreads = 1 (the asynchronous flow is sequential by definition). */
+int oracle_run_ex(int fn, int lattice, int order, int flow, int64_t N, int64_t D, double lb,
+                  double ub, double Cg, double Cp, double Cw, uint64_t seed, uint32_t sid,
+                  const double* o, const double* w, const double* M, int64_t t, int nthreads,
+                  double* X, double* P, double* pF, double* G, int64_t* log_b, double* log_v,
+                  int64_t* log_acc, int64_t* branch)
 {
     if (fn < 0 || fn >= FN_COUNT || N < 1 || D < 1 || t < 0) return -1;
-    if (!(lb < ub) || !(0.0 <= Cg && Cg <= Cp && Cp <= Cw && Cw <= 1.0)) return -2;
+    if (order != 0 && order != 1) return -2;
+    if (flow != 0 && flow != 1) return -2;
+    if (!(lb < ub)) return -2;
+    if (order == 0 && !(0.0 <= Cg && Cg <= Cp && Cp <= Cw && Cw <= 1.0)) return -2;
+    if (order == 1 && !(0.0 <= Cw && Cw <= Cp && Cp <= Cg && Cg <= 1.0)) return -2;
     if (lattice != LATTICE_F64 && lattice != LATTICE_F32) return -3;
     if (lattice == LATTICE_F32 && !(float_at_or_above(lb) <= float_at_or_below(ub))) return -2;
     if ((fn == FN_ELLIPSOID || fn == FN_ROT_ELLIPSOID) && !w) return -4;
@@ -340,10 +389,10 @@ int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
     if (N > 0xffffffffLL || D > 0xffffffffLL || t > 0xffffffffLL || sid >= (1u << 24)) return -5;
     if (nthreads < 1) nthreads = 1;
 
-    /* Eq. 2.1 thresholds on the 32-bit draw. */
-    const uint64_t Tg = (uint64_t)nearbyint(ldexp(Cg, 32));
-    const uint64_t Tp = (uint64_t)nearbyint(ldexp(Cp, 32));
-    const uint64_t Tw = (uint64_t)nearbyint(ldexp(Cw, 32));
+    /* Eq. 2.1 interval ends on the 32-bit draw, in increasing order. */
+    const uint64_t T1 = (uint64_t)nearbyint(ldexp(order ? Cw : Cg, 32));
+    const uint64_t T2 = (uint64_t)nearbyint(ldexp(Cp, 32));
+    const uint64_t T3 = (uint64_t)nearbyint(ldexp(order ? Cg : Cw, 32));
     int64_t nb[4] = { 0, 0, 0, 0 };
 
     /* Generation 0: Kernel Function (I) -- random population; pBest = X0. */
@@ -356,47 +405,77 @@ int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
     int64_t b = 0;
     for (int64_t i = 1; i < N; ++i) if (pF[i] < pF[b]) b = i;
     memcpy(G, P + b * D, (size_t)D * sizeof(double));
+    double gF = pF[b];
     if (log_b) log_b[0] = b;
-    if (log_v) log_v[0] = pF[b];
+    if (log_v) log_v[0] = gF;
     if (log_acc) log_acc[0] = N;
 
     for (int64_t g = 1; g <= t; ++g) {
-        int64_t accepted = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        /* Alg. 2: search for all particles (Eq. 2.1) reading gBest of g-1, then
-         * evaluate (Kernel Function (E)) and update pBests (Alg. 3, "<="). */
+        int64_t accepted = 0;
+        if (flow == 0) {
+            int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            /* Alg. 2: search for all particles (Eq. 2.1) reading gBest of g-1, then
+             * evaluate (Kernel Function (E)) and update pBests (Alg. 3, "<="). */
 #pragma omp parallel for schedule(static) num_threads(nthreads) reduction(+ : accepted, c0, c1, c2, c3)
-        for (int64_t i = 0; i < N; ++i) {
-            double* xi = X + i * D;
-            double* pi = P + i * D;
-            for (int64_t j = 0; j < D; ++j) {
-                uint64_t r = oracle_rho(seed, sid, (uint32_t)g, (uint32_t)i, (uint32_t)j);
-                if (r < Tg) { xi[j] = G[j]; c0++; }
-                else if (r < Tp) { xi[j] = pi[j]; c1++; }
-                else if (r < Tw) { c2++; }
-                else {
-                    xi[j] = oracle_fresh(lattice, seed, sid, TAG_FRESH, (uint32_t)g, (uint32_t)i,
-                                         (uint32_t)j, lb, ub);
-                    c3++;
+            for (int64_t i = 0; i < N; ++i) {
+                double* xi = X + i * D;
+                double* pi = P + i * D;
+                int64_t c[4] = { 0, 0, 0, 0 };
+                stepwise_update(order, lattice, seed, sid, (uint32_t)g, (uint32_t)i, D, lb, ub, T1,
+                                T2, T3, G, pi, xi, c);
+                c0 += c[0]; c1 += c[1]; c2 += c[2]; c3 += c[3];
+                double fi = oracle_fitness(fn, D, xi, o, w, M);
+                if (fi <= pF[i]) {
+                    memcpy(pi, xi, (size_t)D * sizeof(double));
+                    pF[i] = fi;
+                    accepted++;
                 }
             }
-            double fi = oracle_fitness(fn, D, xi, o, w, M);
-            if (fi <= pF[i]) {
-                memcpy(pi, xi, (size_t)D * sizeof(double));
-                pF[i] = fi;
-                accepted++;
+            nb[0] += c0; nb[1] += c1; nb[2] += c2; nb[3] += c3;
+            /* Alg. 4: gBest = lowest-index arg-min over all pBest fitness values. */
+            b = 0;
+            for (int64_t i = 1; i < N; ++i) if (pF[i] < pF[b]) b = i;
+            memcpy(G, P + b * D, (size_t)D * sizeof(double));
+            gF = pF[b];
+        } else {
+            /* Alg. 1: one particle after the other; search, evaluate, then the
+             * pBest and gBest replacements ("<" both), in particle order. */
+            for (int64_t i = 0; i < N; ++i) {
+                double* xi = X + i * D;
+                double* pi = P + i * D;
+                stepwise_update(order, lattice, seed, sid, (uint32_t)g, (uint32_t)i, D, lb, ub, T1,
+                                T2, T3, G, pi, xi, nb);
+                double fi = oracle_fitness(fn, D, xi, o, w, M);
+                if (fi < pF[i]) {
+                    memcpy(pi, xi, (size_t)D * sizeof(double));
+                    pF[i] = fi;
+                    accepted++;
+                    if (fi < gF) {
+                        memcpy(G, xi, (size_t)D * sizeof(double));
+                        gF = fi;
+                        b = i;
+                    }
+                }
             }
         }
-        /* Alg. 4: gBest = lowest-index arg-min over all pBest fitness values. */
-        b = 0;
-        for (int64_t i = 1; i < N; ++i) if (pF[i] < pF[b]) b = i;
-        memcpy(G, P + b * D, (size_t)D * sizeof(double));
-        nb[0] += c0; nb[1] += c1; nb[2] += c2; nb[3] += c3;
         if (log_b) log_b[g] = b;
-        if (log_v) log_v[g] = pF[b];
+        if (log_v) log_v[g] = gF;
         if (log_acc) log_acc[g] = accepted;
     }
     if (branch) for (int k = 0; k < 4; ++k) branch[k] = nb[k];
     return 0;
+}
+
+/* The synchronous run in the default interval order (order 0, flow 0). */
+int oracle_run(int fn, int lattice, int64_t N, int64_t D, double lb, double ub,
+               double Cg, double Cp, double Cw, uint64_t seed, uint32_t sid,
+               const double* o, const double* w, const double* M,
+               int64_t t, int nthreads,
+               double* X, double* P, double* pF, double* G,
+               int64_t* log_b, double* log_v, int64_t* log_acc, int64_t* branch)
+{
+    return oracle_run_ex(fn, lattice, 0, 0, N, D, lb, ub, Cg, Cp, Cw, seed, sid, o, w, M, t,
+                         nthreads, X, P, pF, G, log_b, log_v, log_acc, branch);
 }
 
 /* Maximum OpenMP threads the compiled oracle can use (1 without OpenMP). */

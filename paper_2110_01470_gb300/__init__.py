@@ -31,12 +31,14 @@ PSSO_SPHERE, PSSO_ELLIPSOID, PSSO_RASTRIGIN, PSSO_ROSENBROCK, PSSO_ACKLEY, \
     PSSO_ROT_ELLIPSOID, PSSO_ROT_RASTRIGIN, PSSO_ROT_ACKLEY = range(8)
 PSSO_LATTICE_F64, PSSO_LATTICE_F32 = 0, 1
 PSSO_PREC_F64, PSSO_PREC_F32_RECHECK = 0, 1
+PSSO_ORDER_GPX, PSSO_ORDER_PAPER = 0, 1
 
 FN = {"sphere": PSSO_SPHERE, "ellipsoid": PSSO_ELLIPSOID, "rastrigin": PSSO_RASTRIGIN,
       "rosenbrock": PSSO_ROSENBROCK, "ackley": PSSO_ACKLEY, "rot_ellipsoid": PSSO_ROT_ELLIPSOID,
       "rot_rastrigin": PSSO_ROT_RASTRIGIN, "rot_ackley": PSSO_ROT_ACKLEY}
 LATTICE = {"f64": PSSO_LATTICE_F64, "f32": PSSO_LATTICE_F32}
 PRECISION = {"f64": PSSO_PREC_F64, "f32": PSSO_PREC_F32_RECHECK}
+ORDER = {"gpx": PSSO_ORDER_GPX, "paper": PSSO_ORDER_PAPER}
 
 _STATUS_NAMES = {0: "PSSO_OK", 1: "PSSO_ERR_ARG", 2: "PSSO_ERR_CUDA", 3: "PSSO_ERR_OOM",
                  4: "PSSO_ERR_TIMEOUT", 5: "PSSO_ERR_STATE", 6: "PSSO_ERR_UNSUPPORTED"}
@@ -53,7 +55,7 @@ class psso_problem(ctypes.Structure):
                 ("D", ctypes.c_int64), ("lb", ctypes.c_double), ("ub", ctypes.c_double),
                 ("Cg", ctypes.c_double), ("Cp", ctypes.c_double), ("Cw", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("shift", ctypes.c_void_p),
+                ("order", ctypes.c_uint32), ("shift", ctypes.c_void_p),
                 ("weights", ctypes.c_void_p), ("rotation", ctypes.c_void_p)]
 
 
@@ -208,18 +210,21 @@ def _problems(problems):
         keep += [o, w, M]
         fn = p["fn"]
         lat = p.get("lattice", PSSO_LATTICE_F64)
+        order = p.get("order", PSSO_ORDER_GPX)
         arr[k] = psso_problem(FN[fn] if isinstance(fn, str) else int(fn),
                               LATTICE[lat] if isinstance(lat, str) else int(lat),
                               int(p["N"]), D, float(p["lb"]), float(p["ub"]), float(p["Cg"]),
                               float(p["Cp"]), float(p["Cw"]), int(p["seed"]),
-                              int(p.get("sid", p.get("stream_id", 0))), 0, _ptr(o), _ptr(w),
-                              _ptr(M))
+                              int(p.get("sid", p.get("stream_id", 0))),
+                              ORDER[order] if isinstance(order, str) else int(order),
+                              _ptr(o), _ptr(w), _ptr(M))
     return arr, keep
 
 
 def psso_create_ex(problems, precision=PSSO_PREC_F64, **config):
     """``problems``: list of dicts with keys fn, N, D, lb, ub, Cg, Cp, Cw, seed and
-    optional lattice, sid / stream_id, o / shift, w / weights, M / rotation.
+    optional lattice, sid / stream_id, order ("gpx" / "paper"), o / shift,
+    w / weights, M / rotation.
     ``config``: any psso_config field by name (threads_per_block, log_stride,
     log_capacity, stream, batch_blocks_per_sm, ...)."""
     arr, keep = _problems(problems)

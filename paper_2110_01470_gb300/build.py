@@ -4,6 +4,11 @@ Every ``csrc/*.cu`` translation unit is compiled by nvcc for sm_103a in
 parallel (``gen_variant.cu`` once per kernel variant and width), then linked
 into one shared library next to this file.  Usage:
 ``python -m paper_2110_01470_gb300.build`` or ``build_library()``.
+
+``build_library(trace=True)`` (or ``--trace``) builds a profiling copy instead:
+the same sources compiled with ``-DPSSO_TRACE`` (the persistent kernel then
+stamps ``%globaltimer`` at its phase boundaries, see ``trace_generations``)
+into ``_build/libpsso_trace.so``; the package's own library is untouched.
 """
 from __future__ import annotations
 
@@ -38,11 +43,19 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libpsso.so if any source is newer than it."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+TRACE_OBJDIR = os.path.join(ROOT, "_build", "trace")
+TRACE_LIB = os.path.join(ROOT, "_build", "libpsso_trace.so")
+
+
+def build_library(force: bool = False, verbose: bool = False, trace: bool = False) -> str:
+    """Compile and link libpsso.so if any source is newer than it (with
+    ``trace``: the phase-stamped profiling copy in ``_build/``)."""
+    lib = TRACE_LIB if trace else LIB
+    objdir = TRACE_OBJDIR if trace else OBJDIR
+    flags = NVCC_FLAGS + (["-DPSSO_TRACE"] if trace else [])
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     variant_src = os.path.join(CSRC, "gen_variant.cu")
     jobs = [(src, os.path.basename(src)[:-3], [])
             for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))) if src != variant_src]
@@ -59,12 +72,12 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(job):
         src, name, defs = job
-        obj = os.path.join(OBJDIR, name + ".o")
+        obj = os.path.join(objdir, name + ".o")
         # an object is current when newer than its source and every header
         if not force and os.path.exists(obj) and \
                 os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
             return obj
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
+        cmd = [exe, *ARCH, *flags, *defs, "-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {name}:\n{p.stderr}")
@@ -74,14 +87,14 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, jobs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build_library(force="--force" in sys.argv, verbose=True))
+    print(build_library(force="--force" in sys.argv, verbose=True, trace="--trace" in sys.argv))

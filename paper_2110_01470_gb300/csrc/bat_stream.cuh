@@ -196,9 +196,11 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
                     // the slice's loads first: the draws below do not depend on
                     // them and cover their latency
                     Pos xo[4], po[4], go[4];
-                    ld4(xr + 4 * c, xo);
+                    // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
+                    // swaps them: keep x first, gBest third)
+                    ld4((in.order ? gs : xr) + 4 * c, xo);
                     ld4(prow + 4 * c, po);
-                    ld4(gs + 4 * c, go);
+                    ld4((in.order ? xr : gs) + 4 * c, go);
                     const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
                     uint4 fb = make_uint4(0u, 0u, 0u, 0u);
                     if (sizeof(Pos) == 4)

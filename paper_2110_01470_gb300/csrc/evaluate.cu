@@ -101,11 +101,14 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
     }
     const bool rot = fn >= PSSO_ROT_ELLIPSOID;
     const size_t nM = rot ? (size_t)D * D : 0;
-    std::vector<float> M32(nM);
-    for (size_t q = 0; q < nM; ++q) M32[q] = (float)rotation[q];
+    std::vector<float> M32(2 * nM);   // float(M), then float(M - float(M))
+    for (size_t q = 0; q < nM; ++q) {
+        M32[q] = (float)rotation[q];
+        M32[nM + q] = (float)(rotation[q] - (double)M32[q]);
+    }
     char* dev = nullptr;
     const size_t nx = hx.size(), no = (size_t)Dp * 24, nf = (size_t)N * 16;
-    const size_t mbytes = ((nM * 12 + 255) / 256) * 256;
+    const size_t mbytes = ((nM * 16 + 255) / 256) * 256;
     if (cudaMalloc(&dev, nx + 2 * no + nf + 1024 + mbytes) != cudaSuccess)
         return bad(PSSO_ERR_OOM, "psso_evaluate: cudaMalloc failed");
     double* dM64 = reinterpret_cast<double*>(dev + nx + 2 * no + nf + 1024);
@@ -130,7 +133,7 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
             break;
         }
         if (rot && (cudaMemcpyAsync(dM64, rotation, nM * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                    cudaMemcpyAsync(dM32, M32.data(), nM * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+                    cudaMemcpyAsync(dM32, M32.data(), nM * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
             rc = bad(PSSO_ERR_CUDA, "psso_evaluate: upload failed");
             break;
         }
@@ -147,6 +150,7 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
         in.w32 = weights ? dw32 : nullptr;
         in.M64 = rot ? dM64 : nullptr;
         in.M32 = rot ? dM32 : nullptr;
+        in.M32lo = rot ? dM32 + nM : nullptr;
         const int wpb = 8;
         const unsigned grid = (unsigned)((N + wpb - 1) / wpb);
         if (f32) evaluate_rows<true><<<grid, 32 * wpb, 0, s>>>(in, dX, N, df, derr);

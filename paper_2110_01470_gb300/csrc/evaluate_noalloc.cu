@@ -96,6 +96,9 @@ __device__ void eval_row(const Hot& in, const double* xr, double* f, double* err
                 const double d = j < in.D ? xr[j] : 0.0;
                 x[q][m] = (float)d;
                 exact = exact && ((double)x[q][m] == d);
+                // the FP32 terms use the shift rounded to float; the bound holds for
+                // the FP64 value only when that rounding is exact
+                if (j < in.D) exact = exact && ((double)in.o32[j] == in.o64[j]);
             }
         const Fit32 r = fit32<MAXC>(in, x, lane, 0xffffffffu, 32);
         exact = __all_sync(0xffffffffu, exact);
@@ -151,8 +154,9 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
         set_last_error("psso_evaluate_noalloc: D must be in [1, 1024] (size of the static scratch)");
         return PSSO_ERR_ARG;
     }
-    if (N > ((int64_t)1 << 40)) {
-        set_last_error("psso_evaluate_noalloc: N too large");
+    // one warp per row, 8 rows per block: the grid's x extent must stay below 2^31
+    if (N > (int64_t)8 * 0x7fffffff) {
+        set_last_error("psso_evaluate_noalloc: N above 8 * (2^31 - 1) rows");
         return PSSO_ERR_ARG;
     }
     if (fn >= PSSO_ROT_ELLIPSOID) {
@@ -186,6 +190,8 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
     in.w64 = weights ? s->w64 : nullptr;
     in.w32 = weights ? s->w32 : nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    // clear an earlier, unrelated launch error so that only this call's launches are reported
+    (void)cudaGetLastError();
     fill_scratch<<<(Dp + 255) / 256, 256, 0, cs>>>(s, shift, weights, (int)D, Dp);
     const int wpb = 8;
     const unsigned grid = (unsigned)((N + wpb - 1) / wpb);

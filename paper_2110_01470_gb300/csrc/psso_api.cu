@@ -157,12 +157,15 @@ psso_status check_problem(const psso_problem& pr, int precision, int idx)
     if (pr.D < 1 || pr.D > 32 * MAX_CHUNKS_PER_LANE * 4) return fail(PSSO_ERR_ARG, at + "D must be in [1, 1024]");
     if (!std::isfinite(pr.lb) || !std::isfinite(pr.ub) || !(pr.lb < pr.ub))
         return fail(PSSO_ERR_ARG, at + "bounds must be finite with lb < ub");
-    if (!(0.0 <= pr.Cg && pr.Cg <= pr.Cp && pr.Cp <= pr.Cw && pr.Cw <= 1.0))
+    if (pr.order != PSSO_ORDER_GPX && pr.order != PSSO_ORDER_PAPER)
+        return fail(PSSO_ERR_ARG, at + "unknown interval order");
+    if (pr.order == PSSO_ORDER_GPX && !(0.0 <= pr.Cg && pr.Cg <= pr.Cp && pr.Cp <= pr.Cw && pr.Cw <= 1.0))
         return fail(PSSO_ERR_ARG, at + "need 0 <= Cg <= Cp <= Cw <= 1");
+    if (pr.order == PSSO_ORDER_PAPER && !(0.0 <= pr.Cw && pr.Cw <= pr.Cp && pr.Cp <= pr.Cg && pr.Cg <= 1.0))
+        return fail(PSSO_ERR_ARG, at + "the paper's interval order needs 0 <= Cw <= Cp <= Cg <= 1");
     if (pr.lattice != PSSO_LATTICE_F64 && pr.lattice != PSSO_LATTICE_F32)
         return fail(PSSO_ERR_ARG, at + "unknown lattice");
     if (pr.stream_id >= (1u << 24)) return fail(PSSO_ERR_ARG, at + "stream_id must be < 2^24");
-    if (pr.reserved != 0) return fail(PSSO_ERR_ARG, at + "reserved field must be 0");
     if ((pr.fn == PSSO_ELLIPSOID || pr.fn == PSSO_ROT_ELLIPSOID) && !pr.weights)
         return fail(PSSO_ERR_ARG, at + "ellipsoid functions need weights");
     if (pr.lattice == PSSO_LATTICE_F32 && !(float_at_or_above(pr.lb) <= float_at_or_below(pr.ub)))
@@ -396,9 +399,12 @@ void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
         d.R = I.R;
         d.lattice = I.pr.lattice;
         d.N = I.pr.N;
-        d.Tg = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cg, 32));
+        // thresholds of the first, second and third interval (Eq. 2.1)
+        const bool paper_order = I.pr.order == PSSO_ORDER_PAPER;
+        d.Tg = (uint64_t)std::nearbyint(std::ldexp(paper_order ? I.pr.Cw : I.pr.Cg, 32));
         d.Tp = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cp, 32));
-        d.Tw = (uint64_t)std::nearbyint(std::ldexp(I.pr.Cw, 32));
+        d.Tw = (uint64_t)std::nearbyint(std::ldexp(paper_order ? I.pr.Cg : I.pr.Cw, 32));
+        d.order = paper_order ? 1u : 0u;
         d.k0 = (uint32_t)I.pr.seed;
         d.k1 = (uint32_t)(I.pr.seed >> 32);
         d.sid = I.pr.stream_id;
@@ -415,6 +421,7 @@ void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
         d.w32 = I.w.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_w32);
         d.M64 = I.M.empty() ? nullptr : reinterpret_cast<const double*>(A + I.off_M64);
         d.M32 = I.M.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_M32);
+        d.M32lo = I.M.empty() ? nullptr : reinterpret_cast<const float*>(A + I.off_M32) + I.M.size();
         d.X = A + I.off_X;
         d.P = A + I.off_P;
         d.pf64 = reinterpret_cast<double*>(A + I.off_pf64);
@@ -775,7 +782,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.off_w64 = take(I.w.empty() ? 0 : (size_t)I.Dp * 8);
         I.off_w32 = take(I.w.empty() ? 0 : (size_t)I.Dp * 4);
         I.off_M64 = take(I.M.size() * 8);
-        I.off_M32 = take(I.M.size() * 4);
+        I.off_M32 = take(I.M.size() * 8);   // float(M), then float(M - float(M))
     }
     h->arena_size = align_up(off, 256);
     cudaError_t e = cudaMalloc(&h->arena, h->arena_size);
@@ -832,14 +839,17 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
             h->h2d += (int64_t)(nd * 12);
         }
         if (!I.M.empty()) {
-            staging.emplace_back(I.M.size() * 4);
+            staging.emplace_back(I.M.size() * 8);
             float* m32 = reinterpret_cast<float*>(staging.back().data());
-            for (size_t q = 0; q < I.M.size(); ++q) m32[q] = (float)I.M[q];
+            for (size_t q = 0; q < I.M.size(); ++q) {
+                m32[q] = (float)I.M[q];
+                m32[I.M.size() + q] = (float)(I.M[q] - (double)m32[q]);
+            }
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(h->arena + I.off_M64, I.M.data(), I.M.size() * 8, cudaMemcpyHostToDevice, h->stream);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h->arena + I.off_M32, m32, I.M.size() * 4, cudaMemcpyHostToDevice, h->stream);
-            h->h2d += (int64_t)(I.M.size() * 12);
+                e = cudaMemcpyAsync(h->arena + I.off_M32, m32, I.M.size() * 8, cudaMemcpyHostToDevice, h->stream);
+            h->h2d += (int64_t)(I.M.size() * 16);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -80,8 +80,10 @@ struct InstDev {
     int32_t fn, D, Dp, nchunks;   // Dp = D rounded up to 4; nchunks = Dp / 4
     int32_t G, maxc, R, lattice;  // lanes per particle, chunks per lane, blocks, lattice
     int64_t N;
-    uint64_t Tg, Tp, Tw;          // Eq. 2.1 thresholds on a 32-bit draw (0 .. 2^32)
-    uint32_t k0, k1, sid, pad0;   // Philox key and stream id
+    uint64_t Tg, Tp, Tw;          // Eq. 2.1 thresholds on a 32-bit draw (0 .. 2^32), in
+                                  // increasing order: the first, second and third interval
+    uint32_t k0, k1, sid;         // Philox key and stream id
+    uint32_t order;               // 0: intervals gBest, pBest, keep; 1: keep, pBest, gBest
     double lb, ub, span;          // FP64 lattice: span = ub - lb
     float S32, L32, lbf, ubf;     // FP32 lattice
     const double* o64;            // shift (never null; zeros for "no shift")
@@ -89,7 +91,8 @@ struct InstDev {
     const double* w64;            // ellipsoid weights or null
     const float* w32;
     const double* M64;            // rotation [D][D] (rotated functions) or null
-    const float* M32;
+    const float* M32;             // M rounded to float
+    const float* M32lo;           // float(M - M32): M = M32 + M32lo to about 2^-48 |M|
     void* X;                      // positions  [N][Dp] (float or double)
     void* P;                      // pBests     [N][Dp]
     double* pf64;                 // pBest fitness in FP64 (F32 mode: valid iff pflag)

@@ -65,6 +65,13 @@ __global__ void set_gen(RotCtl* ctl, long long g)
     ctl->rck = 0;
 }
 
+// List entries with this bit set are accepted pBests (P = X) whose value
+// only needs a tighter interval: no decision is left, only the X row is
+// re-evaluated (N < 2^31, so the index fits the other 31 bits).
+constexpr int32_t TIGHTEN = (int32_t)0x80000000u;
+__device__ __forceinline__ int32_t entry_index(int32_t v) { return v & 0x7fffffff; }
+__device__ __forceinline__ bool entry_tighten(int32_t v) { return v < 0; }
+
 // ---- 1. update --------------------------------------------------------------
 template <int MAXC>
 __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
@@ -93,9 +100,11 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
             const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
             const uint4 fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
             float xo[4], po[4], go[4];
-            ld4(xr + 4 * c, xo);
+            // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
+            // swaps them: keep x first, gBest third)
+            ld4((in.order ? gs : xr) + 4 * c, xo);
             ld4(pr + 4 * c, po);
-            ld4(gs + 4 * c, go);
+            ld4((in.order ? xr : gs) + 4 * c, go);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const uint32_t w = word_of(rb, m);
@@ -300,6 +309,9 @@ __global__ void rot_decide(const RotDev r)
         }
         if (lane == 0) {
             if (undecided) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i;
+            // an accepted value whose GEMM bounds are too wide for 1e-6 relative
+            // goes to the refinement too, marked: only its X row is refined
+            if (write && too_wide(r.fn, lo, hi)) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i | TIGHTEN;
             if (accept) atomicAdd(&blk_acc, 1ull);
         }
     }
@@ -334,8 +346,8 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         const int jb = (int)(it % nJb);
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
-        const int32_t i = r.list1[e];
-        if (row == 1 && (d.pflag[i] & 1u)) continue;     // uniform over the block
+        const int32_t i = entry_index(r.list1[e]);
+        if (row == 1 && (entry_tighten(r.list1[e]) || (d.pflag[i] & 1u))) continue;   // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
         __syncthreads();
         for (int k = threadIdx.x; k < D; k += blockDim.x) {
@@ -417,15 +429,94 @@ __device__ Fit32 fit_refined(const RotDev& r, const InstDev& d, const float* z, 
     return rot_final(fn, d.D, s, s2, e, eq, (float)(4 * MAXC + 5 + 2));
 }
 
+// Interval of f(z) for an accepted pBest whose value needs tightening: the
+// fitness evaluated in FP64 on the refined z~ (its rounding is below
+// 2^-40 (|f| + sum t) at these sizes), widened by the effect of z's error
+// ez: sum |t'(xi)| ez over the terms (ellipsoid w (2|z~| + ez) ez; Rastrigin
+// (2 xi + 20 pi min(1, 2 pi xi)) ez, xi = |z~| + ez; Ackley through the
+// bounds on S1 = sum z^2 and Q = sum sin^2(pi z) as in rot_final).  With the
+// refinement's ez near u |z| this is a few u relative: far tighter than the
+// FP32 evaluation's own rounding bound.
+template <int MAXC>
+__device__ void tight_interval(const RotDev& r, const InstDev& d, const float* z, const float* ez, int lane,
+                               float& lo, float& hi)
+{
+    const int fn = base_fn(r.fn);
+    Hot hz = hot_of(d);
+    hz.fn = fn;             // the rows hold z already: the unrotated function with o = 0
+    hz.o64 = r.zero64;
+    const double f = fit64_row<float>(hz, z, false);
+    float e = 0.f, eq = 0.f, s1 = 0.f, at = 0.f;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane + 32 * q;
+        if (c >= d.nchunks) continue;
+        float zv[4], ev[4];
+        ld4(z + 4 * c, zv);
+        ld4(ez + 4 * c, ev);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * c + m;
+            if (j >= d.D) break;
+            const float az = fabsf(zv[m]), ezj = ev[m], xi = az + ezj;
+            if (fn == FN_ELLIPSOID) {
+                const float w = __ldg(r.inst_w32 + j);
+                e = __fadd_ru(e, 1.01f * w * (2.f * az + ezj) * ezj);
+                at = __fadd_ru(at, 1.01f * w * xi * xi);
+            } else if (fn == FN_RASTRIGIN) {
+                e = __fadd_ru(e, 1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ezj);
+                at = __fadd_ru(at, xi * xi + 20.f);
+            } else {   // Ackley
+                e = __fadd_ru(e, 1.01f * (2.f * az + ezj) * ezj);
+                eq = __fadd_ru(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ezj);
+                s1 = __fadd_rn(s1, __fmul_rn(zv[m], zv[m]));
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        e = __fadd_ru(e, __shfl_xor_sync(0xffffffffu, e, off));
+        eq = __fadd_ru(eq, __shfl_xor_sync(0xffffffffu, eq, off));
+        s1 = __fadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, off));
+        at = __fadd_ru(at, __shfl_xor_sync(0xffffffffu, at, off));
+    }
+    float E;
+    if (fn != FN_ACKLEY) {
+        E = 1.1f * e + 0x1p-40f * (at + (float)fabs(f));
+    } else {
+        // S1 from the float sum: at most (K + L + 2) u relative off, K <= 32, L = 5
+        const float Df = (float)d.D;
+        const float s1lo = s1 * (1.f - 48.f * 0x1p-24f);
+        const float f1 = 1.0001f * -20.f * expm1_f32(-0.2f * __fsqrt_rn(s1 / Df));
+        const float d1 = (e <= 0.5f * s1lo) ? 1.5f * f1 * e / s1lo : 4.f * __fsqrt_ru(e / Df);
+        E = 1.1f * (d1 + (2.f * 2.7182818f / Df) * eq) + 0x1p-40f * ((float)fabs(f) + 25.f);
+    }
+    lo = f64_to_f32_rd(f - (double)E);
+    hi = f64_to_f32_ru(f + (double)E);
+}
+
 template <int MAXC>
 __device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int lane)
 {
-    const int32_t i = r.list1[e];
+    const int32_t raw = r.list1[e];
+    const int32_t i = entry_index(raw);
     const int64_t g = r.ctl->gen;
     const size_t ox = (size_t)(2 * e) * d.Dp, op = ox + d.Dp;
+    float plo = d.plo[i], phi = d.phi[i];
+    if (entry_tighten(raw)) {   // accepted already: intersect the two bounds of f(P) = f(X)
+        float tlo, thi;
+        tight_interval<MAXC>(r, d, r.z32 + ox, r.ez32 + ox, lane, tlo, thi);
+        plo = fmaxf(plo, tlo);
+        phi = fminf(phi, thi);
+        if (lane == 0) {
+            d.plo[i] = plo;
+            d.phi[i] = phi;
+            if (too_wide(r.fn, plo, phi)) r.list3[atomicAdd(&r.ctl->n3, 1u)] = raw;
+            atomicAdd(&r.ctl->refined, 1ull);
+        }
+        return;
+    }
     const Fit32 fx = fit_refined<MAXC>(r, d, r.z32 + ox, r.ez32 + ox, lane);
     const float lox = __fsub_rd(fx.f, fx.E), hix = __fadd_ru(fx.f, fx.E);
-    float plo = d.plo[i], phi = d.phi[i];
     const bool have_p = (d.pflag[i] & 1u) != 0;
     if (!have_p) {       // the pBest's interval, tightened the same way (intersection of two bounds)
         const Fit32 fp = fit_refined<MAXC>(r, d, r.z32 + op, r.ez32 + op, lane);
@@ -503,8 +594,9 @@ __global__ void rot_z64(const RotDev r, int which)
         const int jb = (int)(it % nJb);
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
-        const int32_t i = which == 1 ? r.list3[e] : r.list2[e];
-        const bool needed = which == 1 ? (row == 0 || !(d.pflag[i] & 1u)) : row == 1;
+        const int32_t raw = which == 1 ? r.list3[e] : r.list2[e];
+        const int32_t i = entry_index(raw);
+        const bool needed = which == 1 ? (row == 0 || (!entry_tighten(raw) && !(d.pflag[i] & 1u))) : row == 1;
         if (!needed) continue;          // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
         __syncthreads();
@@ -532,7 +624,17 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
     const int64_t g = r.ctl->gen;
     const double* zx = r.zbuf + (size_t)(2 * e) * d.Dp;
     const double* zp = zx + d.Dp;
-    if (which == 1) {
+    if (which == 1 && entry_tighten(r.list3[e])) {   // accepted pBest: its exact value
+        const int32_t i = entry_index(r.list3[e]);
+        const double fx = fit64_row<double>(hz, zx, false);
+        if (lane == 0) {
+            d.pf64[i] = fx;
+            d.pflag[i] = 1u;
+            d.plo[i] = f64_to_f32_rd(fx);
+            d.phi[i] = f64_to_f32_ru(fx);
+            atomicAdd(&r.ctl->rck, 1ull);
+        }
+    } else if (which == 1) {
         const int32_t i = r.list3[e];
         const bool have_p = (d.pflag[i] & 1u) != 0;
         const double fx = fit64_row<double>(hz, zx, false);

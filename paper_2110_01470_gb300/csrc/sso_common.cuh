@@ -96,6 +96,7 @@ struct Hot {
     uint32_t Tg32, Tp32, Tw32;    // thresholds, saturated at 2^32 - 1
     uint32_t tfull;               // bit 0/1/2: Tg/Tp/Tw equal 2^32 (always taken)
     uint32_t k0, k1, sid;
+    uint32_t order;               // 1: Eq. 2.1 as printed (first interval keeps x, third takes gBest)
     float S32, L32, lbf, ubf;
     double lb, ub, span;
     const double* o64;
@@ -104,6 +105,7 @@ struct Hot {
     const float* w32;
     const double* M64;   // rotation, row-major D x D (rotated functions only)
     const float* M32;    // the same rounded to float
+    const float* M32lo;  // float(M - M32) (the compensated FP32 rotation)
 };
 
 __device__ __forceinline__ Hot hot_of(const InstDev& d)
@@ -115,11 +117,11 @@ __device__ __forceinline__ Hot hot_of(const InstDev& d)
     h.Tw32 = d.Tw >= 0x100000000ULL ? 0xffffffffu : (uint32_t)d.Tw;
     h.tfull = (d.Tg >= 0x100000000ULL ? 1u : 0u) | (d.Tp >= 0x100000000ULL ? 2u : 0u) |
               (d.Tw >= 0x100000000ULL ? 4u : 0u);
-    h.k0 = d.k0; h.k1 = d.k1; h.sid = d.sid;
+    h.k0 = d.k0; h.k1 = d.k1; h.sid = d.sid; h.order = d.order;
     h.S32 = d.S32; h.L32 = d.L32; h.lbf = d.lbf; h.ubf = d.ubf;
     h.lb = d.lb; h.ub = d.ub; h.span = d.span;
     h.o64 = d.o64; h.o32 = d.o32; h.w64 = d.w64; h.w32 = d.w32;
-    h.M64 = d.M64; h.M32 = d.M32;
+    h.M64 = d.M64; h.M32 = d.M32; h.M32lo = d.M32lo;
     return h;
 }
 
@@ -458,6 +460,110 @@ __device__ __forceinline__ void rot_matvec32(const Hot& in, const float (&x)[MAX
         }
 }
 
+// Compensated FP32 z = M d for the FP32 fitness of the rotated functions:
+// d = x - o exactly as a float pair (TwoSum; x and o are floats), M as the
+// float pair M32 + M32lo, and for every output the Dot2 recurrence of Ogita,
+// Rump and Oishi ("Accurate sum and dot product", SISC 2005) over k ascending:
+// TwoProduct of M32 d_hi, TwoSum into p, the two rounding errors and the cross
+// terms M32 d_lo + M32lo d_hi into s; z = p + s.  With n = D + 8 and
+// g = gamma_n, |z~ - z| <= 1.01 u |z~| + (2 g^2 + 4 u g + 2^-42) S, S =
+// sum |M||d| <= S~ (1 + 2 gamma_D)(1 + 2^-22) from the FP32 sum S~ of
+// |M32||d_hi|; the 2^-42 S also covers the FP64 oracle's own rounding of z.
+// About 16 FP32 operations per term against 2 for a plain fma chain, and a
+// bound near u |z| instead of D u sum |M||d|: an FP32 rotated fitness within a
+// few u of the FP64 value, and far fewer FP64 rechecks.
+template <int MAXC>
+__device__ __noinline__ void rot_matvec32c_impl(const Hot& in, const RowBuf<float, MAXC>& xb, int lane_g,
+                                                unsigned gmask, int G, RowBuf<float, MAXC>& zb,
+                                                RowBuf<float, MAXC>& eb)
+{
+    const auto& x = xb.v;
+    auto& z = zb.v;
+    auto& ez = eb.v;
+    const int D = in.D;
+    float dh[MAXC][4], dl[MAXC][4], p[MAXC][4], sc[MAXC][4], S[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * (lane_g + 32 * q) + m;
+            const float a = (j < D) ? x[q][m] : 0.f, b = (j < D) ? -__ldg(in.o32 + j) : 0.f;
+            const float sum = __fadd_rn(a, b);
+            const float bb = __fsub_rn(sum, a);
+            dh[q][m] = sum;
+            dl[q][m] = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+            p[q][m] = 0.f;
+            sc[q][m] = 0.f;
+            S[q][m] = 0.f;
+        }
+#pragma unroll
+    for (int qk = 0; qk < MAXC; ++qk) {
+        for (int l = 0; l < G; ++l) {
+            if (128 * qk + 4 * l >= D) break;
+#pragma unroll
+            for (int mk = 0; mk < 4; ++mk) {
+                const int k = 128 * qk + 4 * l + mk;
+                const float bh = __shfl_sync(gmask, dh[qk][mk], l, G);
+                const float bl = __shfl_sync(gmask, dl[qk][mk], l, G);
+                if (k < D) {
+                    const float abh = fabsf(bh);
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int j = 4 * (lane_g + 32 * q) + m;
+                            if (j < D) {
+                                const size_t o = (size_t)j * D + k;
+                                const float a = __ldg(in.M32 + o), al = __ldg(in.M32lo + o);
+                                const float h = __fmul_rn(a, bh);
+                                const float r = __fmaf_rn(a, bh, -h);        // a bh = h + r exactly
+                                const float t = __fadd_rn(p[q][m], h);
+                                const float bb = __fsub_rn(t, p[q][m]);
+                                const float e = __fadd_rn(__fsub_rn(p[q][m], __fsub_rn(t, bb)), __fsub_rn(h, bb));
+                                p[q][m] = t;                                   // p + h = t + e exactly
+                                const float cross = __fmaf_rn(a, bl, __fmul_rn(al, bh));
+                                sc[q][m] = __fadd_rn(sc[q][m], __fadd_rn(__fadd_rn(e, r), cross));
+                                S[q][m] = __fmaf_rn(fabsf(a), abh, S[q][m]);
+                            }
+                        }
+                }
+            }
+        }
+    }
+    const float U = 0x1p-24f;
+    const float nl = (float)(D + 8);
+    const float gam = nl * U / (1.f - nl * U);
+    const float gD = (float)D * U / (1.f - (float)D * U);
+    const float cS = 1.01f * (2.f * gam * gam + 4.f * U * gam + 0x1p-42f) * (1.f + 2.f * gD) * (1.f + 0x1p-22f);
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            z[q][m] = __fadd_rn(p[q][m], sc[q][m]);
+            ez[q][m] = __fmaf_ru(cS, S[q][m], 1.01f * U * fabsf(z[q][m]));
+        }
+}
+
+template <int MAXC>
+__device__ __forceinline__ void rot_matvec32c(const Hot& in, const float (&x)[MAXC][4], int lane_g,
+                                              unsigned gmask, int G, float (&z)[MAXC][4],
+                                              float (&ez)[MAXC][4])
+{
+    RowBuf<float, MAXC> xb, zb, eb;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+    rot_matvec32c_impl<MAXC>(in, xb, lane_g, gmask, G, zb, eb);
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            z[q][m] = zb.v[q][m];
+            ez[q][m] = eb.v[q][m];
+        }
+}
+
 template <int MAXC, bool ROT>
 __device__ __forceinline__ Fit32 fit32_impl(const Hot& in, const float (&x)[MAXC][4], int lane_g,
                                             unsigned gmask, int G)
@@ -466,7 +572,7 @@ __device__ __forceinline__ Fit32 fit32_impl(const Hot& in, const float (&x)[MAXC
     const bool rot = ROT && is_rotated(in.fn);
     const int fn = base_fn(in.fn);
     float zr[MAXC][4], ezr[MAXC][4];
-    if (rot) rot_matvec32<MAXC>(in, x, lane_g, gmask, G, zr, ezr);
+    if (rot) rot_matvec32c<MAXC>(in, x, lane_g, gmask, G, zr, ezr);
     float acc = 0.f, acc2 = 0.f, accE = 0.f, accZ = 0.f;
     float rS1 = 0.f, rQ = 0.f;   // rotated: absolute error bounds of S1 and Q (Ackley)
 #pragma unroll
@@ -665,6 +771,16 @@ __device__ __forceinline__ Fit32 fit32(const Hot& in, const float (&x)[MAXC][4],
         return fit32_rotated<MAXC>(in, xb, lane_g, gmask, G);
     }
     return fit32_impl<MAXC, false>(in, x, lane_g, gmask, G);
+}
+
+// True when the interval [lo, hi] of a fitness value is too wide for its
+// midpoint to lie within 0.9e-6 relative of the value (relative to
+// max(|f|, 1e-6 (20 + e)) for Ackley, whose optimum is 0, else to |f|; every
+// test function is >= 0).
+__device__ __forceinline__ bool too_wide(int fn, float lo, float hi)
+{
+    const float floor = (base_fn(fn) == FN_ACKLEY) ? 1e-6f * 22.7182818f : 0.f;
+    return __fsub_ru(hi, lo) > 1.8e-6f * fmaxf(lo, floor);
 }
 
 // ---------------------------------------------------------------------------

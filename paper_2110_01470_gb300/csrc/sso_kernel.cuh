@@ -408,9 +408,11 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
                 if (sizeof(Pos) == 4)
                     fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
                 Pos xo[4], po[4], go[4];
-                ld4(xr + 4 * c, xo);
+                // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
+                // swaps them: keep x first, gBest third)
+                ld4((in.order ? gs : xr) + 4 * c, xo);
                 ld4(pr + 4 * c, po);
-                ld4(gs + 4 * c, go);
+                ld4((in.order ? xr : gs) + 4 * c, go);
                 uint32_t nf = 0;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -463,8 +465,14 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
         s.has64 = 0;
         s.f64v = 0.0;
         s.wstate = true;
+        // A rotated function's accepted value whose bounds are too wide to place
+        // it within 1e-6 of the FP64 value is made exact at commit (the decision
+        // itself is certain): the pBest fitness of an FP32 run stays within 1e-6
+        // relative of the FP64 oracle's.
+        const bool tighten = is_rotated(in.fn) && too_wide(in.fn, s.lo, s.hi);
         if (g == 0) {
-            s.accept = true;
+            s.accept = !tighten;
+            s.undecided = tighten;
         } else {
             const float plo = v.plo[e], phi = v.phi[e];
             const uint32_t pfl = v.pflag[e];
@@ -474,7 +482,8 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
                 s.wstate = false;
                 s.lo = plo; s.hi = phi; s.has64 = (int)(pfl & 1u); s.f64v = ppf;
             } else if (s.hi < plo) {
-                s.accept = true;
+                s.accept = !tighten;
+                s.undecided = tighten;      // certain accept, value made exact at commit
             } else if (s.lo > phi) {
                 s.accept = false;
                 s.lo = plo; s.hi = phi; s.has64 = (int)(pfl & 1u); s.f64v = ppf;
@@ -544,7 +553,11 @@ __device__ __forceinline__ void particle_commit(const Hot& in, const View<Pos>& 
     }
     if (F32R && s.undecided) {
         __syncwarp(gmask);
-        const Resolved r = resolve_f64<Pos, MAXC>(in, xr, pr, (v.pflag[e] & 1u) != 0, v.pf64[e], lane_g, gmask);
+        // generation 0 has no pBest yet: compare against +inf, i.e. accept
+        const bool g0 = (g == 0);
+        const Resolved r = resolve_f64<Pos, MAXC>(in, xr, pr, g0 || (v.pflag[e] & 1u) != 0,
+                                                  g0 ? __longlong_as_double(0x7ff0000000000000LL) : v.pf64[e],
+                                                  lane_g, gmask);
         s.accept = r.accept;
         s.has64 = 1;
         s.f64v = r.f64v;

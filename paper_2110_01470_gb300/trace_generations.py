@@ -16,7 +16,6 @@ Phase stamps (control warp of a pipelined block): 0 generation start,
 from __future__ import annotations
 
 import ctypes
-import os
 import sys
 
 import numpy as np
@@ -31,10 +30,7 @@ PHASES = [(5, "records of g-1 complete"), (8, "arg-min of the records"), (9, "gB
 
 def build_traced() -> str:
     """Compiles the library with the phase stamps into _build/ (not the package)."""
-    B.NVCC_FLAGS = B.NVCC_FLAGS + ["-DPSSO_TRACE"]
-    B.OBJDIR = os.path.join(B.ROOT, "_build", "trace")
-    B.LIB = os.path.join(B.ROOT, "_build", "libpsso_trace.so")
-    return B.build_library()
+    return B.build_library(trace=True)
 
 
 def main(tpb: int = 0) -> None:

@@ -12,9 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _oracle(p, t):
-    return oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                      p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                      M=p["M"])
+    return oracle.run_problem(p, t)
 
 
 def _states(lib, ps, t, precision, **cfg):

@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import workload
+from helpers import REL_TOL, fitness_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -14,9 +15,7 @@ FNS = ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley"]
 
 
 def _oracle(p, t):
-    return oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                      p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                      M=p["M"])
+    return oracle.run_problem(p, t)
 
 
 def _mixed(lattice, count=20, seed=0):
@@ -76,6 +75,8 @@ def test_fp32_same_decisions(lib):
         assert np.all(lo <= r["log_v"]) and np.all(r["log_v"] <= hi)
         v, b, row = g["best"]
         assert b == r["log_b"][t] and v == r["log_v"][t]
+        rel = fitness_rel_err(g["pF"], r["pF"], p["fn"])
+        assert np.all(rel <= REL_TOL), (p["fn"], rel.max())
 
 
 def test_same_as_persistent_kernel_split_runs(lib):

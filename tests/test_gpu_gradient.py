@@ -266,9 +266,7 @@ def test_polish_zero_steps_keeps_oracle_trajectory(lib, cfg):
         v, b, row = lib.psso_best(h, 0, p["D"])
     finally:
         lib.psso_destroy(h)
-    r = oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                   p["seed"], t1 + t2, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                   M=p["M"])
+    r = oracle.run_problem(p, t1 + t2)
     assert np.array_equal(X, r["X"]) and np.array_equal(P, r["P"]) and np.array_equal(pF, r["pF"])
     assert v == r["log_v"][-1] and b == r["log_b"][-1] and np.array_equal(row, r["G"])
 

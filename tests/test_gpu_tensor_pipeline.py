@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import workload
+from helpers import REL_TOL, fitness_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -14,9 +15,7 @@ ROT = ["rot_ellipsoid", "rot_rastrigin", "rot_ackley"]
 
 
 def _oracle(p, t):
-    return oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                      p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                      M=p["M"])
+    return oracle.run_problem(p, t)
 
 
 def _run(lib, problems, t, chunks=None, **cfg):
@@ -35,9 +34,11 @@ def _run(lib, problems, t, chunks=None, **cfg):
         lib.psso_destroy(h)
 
 
-def _same(g, r, t):
+def _same(g, r, t, fn):
     assert np.array_equal(g["X"], r["X"])
     assert np.array_equal(g["P"], r["P"])
+    rel = fitness_rel_err(g["pF"], r["pF"], fn)
+    assert np.all(rel <= REL_TOL), rel.max()
     log = g["log"]
     assert np.array_equal(log["generation"], np.arange(t + 1))
     assert np.array_equal(log["index"], r["log_b"])
@@ -56,7 +57,7 @@ def _same(g, r, t):
 def test_same_decisions_as_oracle(lib, fn, N, D, t):
     p = workload.problem(fn, N, D, seed=40 + D, lattice="f32", stream=N % 3)
     (g,), st = _run(lib, [p], t)
-    _same(g, _oracle(p, t), t)
+    _same(g, _oracle(p, t), t, fn)
     assert st["blocks"] == 0          # no persistent-kernel blocks: the pipeline ran it
 
 
@@ -65,7 +66,7 @@ def test_split_runs_and_reset(lib):
     t = 24
     r = _oracle(p, t)
     (g,), _ = _run(lib, [p], t, chunks=[1, 7, 16])
-    _same(g, r, t)
+    _same(g, r, t, p["fn"])
     h = lib.psso_create_ex([p], "f32", tensor_rotation=1, log_stride=1, log_capacity=t + 1)
     try:
         lib.psso_run(h, 9)
@@ -108,7 +109,7 @@ def test_mixed_batch(lib):
     t = 15
     outs, st = _run(lib, ps, t)
     for g, p in zip(outs, ps):
-        _same(g, _oracle(p, t), t)
+        _same(g, _oracle(p, t), t, p["fn"])
     assert st["blocks"] > 0
 
 

@@ -157,19 +157,21 @@ def test_bruteforce_grid(fn, D):
     assert best <= gmin + 0.05 * max(1.0, gmin) + 0.05
 
 
-def test_paper_triple_mapping_keeps_branch_probabilities():
-    """Reading of Eq. 2.1's interval order: the paper's Cw < Cp < Cg triple
-    (0.3, 0.6, 0.8; keep x on [0, Cw), pBest on [Cw, Cp), gBest on [Cp, Cg),
-    fresh on [Cg, 1)) is run as cumulative gBest / pBest / keep thresholds with
-    the same branch probabilities.  The paper's widths are computed here from
-    its own order; the oracle's branch counts on the paper workload must match
-    them within 5 sigma."""
+@pytest.mark.parametrize("mapped", [False, True])
+def test_paper_triple_mapping_keeps_branch_probabilities(mapped):
+    """Eq. 2.1's interval order: the paper's Cw < Cp < Cg triple (0.3, 0.6,
+    0.8; keep x on [0, Cw), pBest on [Cw, Cp), gBest on [Cp, Cg), fresh on
+    [Cg, 1)), run in that printed order, and mapped by probability onto the
+    default order (cumulative gBest / pBest / keep thresholds 0.2 / 0.5 /
+    0.8).  The paper's widths are computed here from its own order; the
+    oracle's branch counts must match them within 5 sigma either way."""
     import workload
     cw, cp, cg = 0.3, 0.6, 0.8
     paper = {"keep": cw, "pbest": cp - cw, "gbest": cg - cp, "fresh": 1.0 - cg}
     p = workload.config("paper_rosenbrock_n100")["problems"][0]
-    r = oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"], p["seed"], 20,
-                   o=p["o"])
+    if mapped:
+        p = dict(p, order="gpx", Cg=cg - cp, Cp=cg - cw, Cw=cg)
+    r = oracle.run_problem(p, 20)
     n = r["branch"].sum()
     got = dict(zip(["gbest", "pbest", "keep", "fresh"], r["branch"] / n))
     for k, want in paper.items():

@@ -22,10 +22,9 @@ measured on):
   grad_d256      Rosenbrock and rotated Ackley, D=256, N=4096, t=3000
   paper_rosenbrock_n{100,200,300,350}
                  the paper's timing workload (Table 3.10): Rosenbrock, D=50,
-                 t=1000, bounds [-2.048, 2.048], no shift, FP64; the paper's
-                 interval triple Cw/Cp/Cg = 0.3/0.6/0.8 taken by probability
-                 as cumulative Cg/Cp/Cw = 0.2/0.5/0.8 (same branch
-                 probabilities: gBest 0.2, pBest 0.3, keep 0.3, fresh 0.2)
+                 t=1000, bounds [-2.048, 2.048], no shift, FP64, and the
+                 paper's interval triple Cw/Cp/Cg = 0.3/0.6/0.8 in the interval
+                 order Eq. 2.1 prints (keep, pBest, gBest, fresh)
 """
 from __future__ import annotations
 
@@ -82,8 +81,11 @@ def ellipsoid_weights(D: int):
 
 
 def problem(fn: str, N: int, D: int, *, seed: int = 1, lattice: str = "f64",
-            shift_range=None, bounds=None, Cg=0.4, Cp=0.7, Cw=0.9, stream: int = 0):
-    """A complete problem description (plain dict of data) for one SSO instance."""
+            shift_range=None, bounds=None, Cg=0.4, Cp=0.7, Cw=0.9, stream: int = 0,
+            order: str = "gpx"):
+    """A complete problem description (plain dict of data) for one SSO instance.
+    ``order`` is the interval order of Eq. 2.1: "gpx" (gBest, pBest, keep with
+    Cg <= Cp <= Cw) or "paper" (keep, pBest, gBest with Cw <= Cp <= Cg)."""
     lb, ub = bounds if bounds is not None else BOUNDS[fn]
     if shift_range is None:
         shift_range = (0.8 * lb, 0.8 * ub)
@@ -91,7 +93,7 @@ def problem(fn: str, N: int, D: int, *, seed: int = 1, lattice: str = "f64",
     w = ellipsoid_weights(D) if fn in ("ellipsoid", "rot_ellipsoid") else None
     M = rotation(D, seed, stream) if fn.startswith("rot_") else None
     return dict(fn=fn, N=N, D=D, lb=lb, ub=ub, Cg=Cg, Cp=Cp, Cw=Cw, seed=seed,
-                sid=stream, lattice=lattice, o=o, w=w, M=M)
+                sid=stream, lattice=lattice, order=order, o=o, w=w, M=M)
 
 
 def batched_table(count: int = 512, seed: int = 1, lattice: str = "f32"):
@@ -131,6 +133,6 @@ def config(name: str):
     if name.startswith("paper_rosenbrock_n"):
         N = int(name[len("paper_rosenbrock_n"):])
         p = problem("rosenbrock", N, 50, seed=1, lattice="f64", shift_range=(0.0, 0.0),
-                    Cg=0.2, Cp=0.5, Cw=0.8)
+                    Cg=0.8, Cp=0.6, Cw=0.3, order="paper")
         return dict(problems=[p], t=1000, precision="f64")
     raise KeyError(name)
