@@ -15,7 +15,14 @@ the FP64-fitness path on the same workload is timed beside it.
   e2e     the same metric through the public API with host buffers: create
           (problem data host->device), run, best (result device->host),
           destroy, wall-clock with a device sync on both sides
-  roofline  the persistent generation kernel against the ALU issue peak
+  roofline  the dominant kernel against a measured peak: the persistent
+          generation kernel against the pipe rates psso_microbench measures
+          in the same run (Philox blocks, FP32 / FP64 FMA, issue); the
+          tensor-core GEMM against sustained BF16; the batched step kernel
+          against HBM bandwidth
+  fitness_err_vs_fp64  FP32 fitness against FP64 on the final state (stored
+          pBest values and a raw FP32 evaluation of the same rows)
+  peaks   the psso_microbench record of this GPU
   cpu_baseline  the CPU oracle on the host cores, bounded sample
 
 Multi-GPU: replicas only (one independent swarm per rank, stream id = rank,
@@ -39,9 +46,7 @@ if ROOT not in sys.path:
 
 METRIC = "particle-variable updates/s"
 UNIT = "updates/s"
-SM_COUNT = 152
 LANES_PER_SM = 128            # 4 sub-partitions x 32 lanes, one warp instruction each per clock
-ALU_CLOCK_MHZ = 2070.0        # maximum SM clock of a GB300
 
 
 def parse():
@@ -73,19 +78,67 @@ def philox_blocks_per_update(p):
     return 0.25 + fresh_blocks * (1.0 - p["Cw"] ** 4) / 4.0
 
 
-# 32-bit operations of one fitness term in the FP32 path (see the kernel).
+# Operations of one fitness term: FP32 path (value and error bound) and FP64
+# path (sub, the term's arithmetic, the accumulation; sin(pi z) is a degree-21
+# odd polynomial after the reduction).
 FIT32_OPS = {"sphere": 3, "ellipsoid": 4, "rastrigin": 17, "rosenbrock": 9, "ackley": 19}
+FIT64_OPS = {"sphere": 2, "ellipsoid": 3, "rastrigin": 19, "rosenbrock": 8, "ackley": 18}
+PHILOX_OPS = 80               # per Philox-4x32-10 block: 10 rounds x (2 products, 4 xors, 2 adds)
 
 
-def alu_ops_per_update(p):
-    """Algorithmic 32-bit ALU operations per particle-variable update: Philox
-    (10 rounds x 8 ops), Eq. 2.1 selection (3 compares + select), the fresh-value
-    map (4 ops at rate 1 - Cw), and the FP32 fitness term; a rotated function
-    adds its row of z = M (x - o): D fused multiply-adds per variable."""
+def op_counts(p, prec):
+    """Algorithmic operations per particle-variable update, by pipe: the
+    Philox blocks (80 integer operations each), the Eq. 2.1 selection (3
+    compares + select, integer), the fresh-value map (4 operations at rate
+    1 - Cw, FP32 or FP64 by lattice) and the fitness term (FP32 or FP64 by
+    precision); a rotated function adds its row of z = M (x - o): D fused
+    multiply-adds per variable."""
     base = p["fn"].replace("rot_", "")
     rot = p["D"] if p["fn"].startswith("rot_") else 0
-    return (80.0 * philox_blocks_per_update(p) + 4.0 + 4.0 * (1.0 - p["Cw"])
-            + FIT32_OPS[base] + rot)
+    fresh = 4.0 * (1.0 - p["Cw"])
+    c = {"philox_blocks": philox_blocks_per_update(p), "int": 4.0, "fp32": 0.0, "fp64": 0.0}
+    c["fp32" if p["lattice"] == "f32" else "fp64"] += fresh
+    if prec == "f32":
+        c["fp32"] += FIT32_OPS[base] + rot
+    else:
+        c["fp64"] += FIT64_OPS[base] + rot
+    return c
+
+
+def alu_ops_per_update(p, prec="f32"):
+    c = op_counts(p, prec)
+    return PHILOX_OPS * c["philox_blocks"] + c["int"] + c["fp32"] + c["fp64"]
+
+
+def alu_roofline(problems, t, prec, kernel_s, peaks, kernel):
+    """Roofline of a generation kernel bound by arithmetic, against the
+    measured pipe rates of this GPU (psso_microbench): the shortest time the
+    work can take is the largest of Philox blocks / measured Philox rate,
+    FP32 operations / measured FP32 FMA rate, FP64 operations / measured FP64
+    FMA rate and all operations / issue rate (128 lanes per SM and clock at
+    the measured SM clock).  peak = operations / that time, so frac = that
+    time / the kernel's time."""
+    tot = {"philox_blocks": 0.0, "int": 0.0, "fp32": 0.0, "fp64": 0.0}
+    for p in problems:
+        u = p["N"] * p["D"] * t
+        for k, v in op_counts(p, prec).items():
+            tot[k] += v * u
+    ops = PHILOX_OPS * tot["philox_blocks"] + tot["int"] + tot["fp32"] + tot["fp64"]
+    issue = peaks["sms"] * LANES_PER_SM * peaks["sm_clock_mhz"] * 1e6
+    times = {"philox": tot["philox_blocks"] / peaks["philox_blocks_per_s"],
+             "fp32": tot["fp32"] / peaks["fp32_fma_per_s"],
+             "fp64": tot["fp64"] / peaks["fp64_fma_per_s"],
+             "issue": ops / issue}
+    limiter = max(times, key=times.get)
+    t_roof = times[limiter]
+    upd = sum(p["N"] * p["D"] for p in problems) * t
+    return {"bound": "alu", "achieved": ops / kernel_s / 1e12, "peak": ops / t_roof / 1e12,
+            "unit": "Tops/s", "frac": t_roof / kernel_s, "limiter": limiter,
+            "kernel": kernel, "kernel_ms_per_launch": kernel_s * 1e3,
+            "ops_per_update": ops / upd, "roofline_ms": t_roof * 1e3,
+            "pipe_ms": {k: v * 1e3 for k, v in times.items()},
+            "peak_note": "measured by psso_microbench in this run (Philox-4x32-10 blocks, FP32 / FP64 "
+                         "FMA chains, SM clock); achieved counts algorithmic operations"}
 
 
 # ---------------------------------------------------------------------------
@@ -156,9 +209,7 @@ def cpu_baseline(problems, t_full, seconds):
 
     def run(t):
         t0 = time.perf_counter()
-        oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                   p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                   M=p["M"], nthreads=threads)
+        oracle.run_problem(p, t, nthreads=threads)
         return time.perf_counter() - t0
 
     probe = run(2)
@@ -178,6 +229,7 @@ def run_reference(args):
         return
     import oracle
     import workload
+    live = psso.psso_microbench(sptr_of(torch))   # measured pipe / latency peaks of this GPU
     cfg = workload.config(args.workload)
     p = cfg["problems"][0]
     threads = max(1, os.cpu_count() or 1)
@@ -187,9 +239,7 @@ def run_reference(args):
 
     def one(t):
         t0 = time.perf_counter()
-        oracle.run(p["fn"], p["N"], p["D"], p["lb"], p["ub"], p["Cg"], p["Cp"], p["Cw"],
-                   p["seed"], t, lattice=p["lattice"], sid=p["sid"], o=p["o"], w=p["w"],
-                   M=p["M"], nthreads=threads)
+        oracle.run_problem(p, t, nthreads=threads)
         return time.perf_counter() - t0
 
     per_gen = max(one(2) / 3.0, 1e-6)
@@ -238,12 +288,32 @@ def job_rate(units_per_step, steps, world, max_total_ms):
     return units_per_step * steps * world / (max_total_ms / 1e3)
 
 
-GEMM_TRAFFIC_BYTES = {(8192, 1000): 56.755712e6 + 1.514752e6}
-# DRAM bytes (read + write) of one launch of the persistent kernel, from an
-# ncu capture of the kernel as it stands, keyed by (fn, N, D, t, precision).
-# Empty: the last capture (profiles/sso_generations_rastrigin_d100.md, 1.86 MB
-# per 5000-generation launch) predates the current revision of the kernel.
-GEN_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# the kernel as it stands, keyed by (kernel, workload); each entry carries the
+# digest of the kernel's sources at capture time and is reported only while
+# the sources still match (a changed kernel reports traffic null).
+TRAFFIC = {
+    ("rot_gemm_fit", "rotated_d1000"): ("", 56.755712e6 + 1.514752e6),
+    ("sso_generations", "rastrigin_d100"): ("", None),
+}
+KERNEL_SOURCES = {
+    "rot_gemm_fit": ["tc_gemm.cuh", "rot_pipeline.cu", "sso_common.cuh", "devmath.cuh"],
+    "sso_generations": ["sso_kernel.cuh", "sso_common.cuh", "devmath.cuh", "gen_variant.cu"],
+}
+
+
+def source_digest(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2110_01470_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(kernel, workload):
+    digest, nbytes = TRAFFIC.get((kernel, workload), ("", None))
+    return nbytes if digest and digest == source_digest(kernel) else None
 
 
 def measured_peaks():
@@ -254,14 +324,15 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def tensor_roofline(psso, problems, prec, sptr, gens=20):
-    """Rotated workloads on the tensor-core pipeline: per-kernel event timing
-    of one instance (psso_time_kernels) and the roofline of the GEMM kernel.
-    Algorithmic work is z = M (x - o): 2 N D^2 flops per generation; the
-    kernel executes six BF16 products over the padded extents."""
-    p = problems[0]
-    if prec != "f32" or not p["fn"].startswith("rot_") or p["N"] < 128 or p["D"] < 32:
+def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
+    """Rotated swarms on the tensor-core pipeline: per-kernel event timing of
+    the first such instance (psso_time_kernels) and the roofline of the GEMM
+    kernel.  Algorithmic work is z = M (x - o): 2 N D^2 flops per generation;
+    the kernel executes six BF16 products over the padded extents."""
+    rot = [p for p in problems if p["fn"].startswith("rot_") and p["N"] >= 128 and p["D"] >= 32]
+    if prec != "f32" or not rot:
         return None
+    p = rot[0]
     h = psso.psso_create_ex([p], prec, stream=sptr)
     try:
         psso.psso_run(h, gens)
@@ -274,11 +345,8 @@ def tensor_roofline(psso, problems, prec, sptr, gens=20):
     peaks, which = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     achieved = 2.0 * N * D * D / t / 1e12
-    # DRAM bytes per launch of rot_gemm_fit at N=8192, D=1000 from one ncu capture
-    # (profiles/rot_gemm_fit_rotated_d1000.md); valid for that shape and this kernel
-    traffic = GEMM_TRAFFIC_BYTES.get((N, D))
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": traffic_of("rot_gemm_fit", workload),
             "traffic_algorithmic": 2 * 3 * (Np + Jp) * Kp,
             "kernel": "rot_gemm_fit (tcgen05 split-BF16 GEMM + fitness epilogue)",
             "kernel_ms_per_launch": ms["gemm_fit"],
@@ -287,6 +355,115 @@ def tensor_roofline(psso, problems, prec, sptr, gens=20):
                          "achieved counts 2 N D^2 algorithmic flops, executed_tflops the six split "
                          "BF16 products over padded extents",
             "kernels_ms": ms, "instance": {"fn": p["fn"], "N": N, "D": D}}
+
+
+def accept_rate(psso, problems, prec, t, sptr, stride=10):
+    """Mean pBest accept rate alpha per instance over a plain run of t
+    generations (from the per-generation log, every `stride`-th generation)."""
+    h = psso.psso_create_ex(problems, prec, stream=sptr, log_stride=stride,
+                            log_capacity=t // stride + 2)
+    try:
+        psso.psso_run(h, t)
+        out = []
+        for k, p in enumerate(problems):
+            log = psso.psso_get_log(h, k)
+            sel = log["generation"] > 0
+            acc = log["accepted"][sel]
+            out.append(float(acc.mean()) / p["N"] if acc.size else 0.0)
+        return out
+    finally:
+        psso.psso_destroy(h)
+
+
+def batched_roofline(psso, problems, prec, t, sptr, live, gens=20):
+    """Batched pipeline: per-kernel event timing (psso_time_kernels) and the
+    HBM roofline of the dominant step kernel.  Algorithmic bytes per update
+    (FP32 positions): write x 4, read the selected source 2 (x with
+    probability Cw - Cp, pBest Cp - Cg: 0.2 + 0.3 of 4 bytes), write the pBest
+    row 4 alpha -> 6 + 4 alpha; sector-granular compulsory traffic reads x and
+    P whole: 12 + 4 alpha.  The whole step's bound is the larger of all bytes /
+    HBM and all operations / the measured ALU rate (instances run
+    concurrently, so their times do not add)."""
+    alpha = accept_rate(psso, problems, prec, t, sptr)
+    h = psso.psso_create_ex(problems, prec, stream=sptr)
+    try:
+        psso.psso_run(h, 3)
+        ms = psso.psso_time_batch_kernels(h, gens)
+    finally:
+        psso.psso_destroy(h)
+    stream_upd = step_upd = 0.0
+    b_alg = {"stream": 0.0, "step": 0.0}
+    b_cmp = {"stream": 0.0, "step": 0.0}
+    for p, a in zip(problems, alpha):
+        u = p["N"] * p["D"]
+        kind = "stream" if (p["D"] > 128 and not p["fn"].startswith("rot_")) else "step"
+        b_alg[kind] += u * (6.0 + 4.0 * a)
+        b_cmp[kind] += u * (12.0 + 4.0 * a)
+        if kind == "stream":
+            stream_upd += u
+        else:
+            step_upd += u
+    hbm = peaks["hbm_gbs"] * 1e9
+    dom = "stream" if ms["stream"] >= ms["step"] else "step"
+    t_dom = ms[dom] / 1e3
+    ops_all = sum(alu_ops_per_update(p, prec) * p["N"] * p["D"] for p in problems)
+    alu = alu_roofline(problems, 1, prec, 1.0, live, "")
+    alu_rate = alu["peak"] * 1e12
+    peaks, which = measured_peaks()
+    gen_s = (ms["stream"] + ms["step"] + ms["argmin"]) / 1e3
+    t_all = max((b_alg["stream"] + b_alg["step"]) / hbm, ops_all / alu_rate)
+    t_all_c = max((b_cmp["stream"] + b_cmp["step"]) / hbm, ops_all / alu_rate)
+    # the survey's sum over instances of max(bytes / HBM, ops / ALU), for reference
+    t_sum_max = sum(max(p["N"] * p["D"] * (6.0 + 4.0 * a) / hbm,
+                        alu_ops_per_update(p, prec) * p["N"] * p["D"] / alu_rate)
+                    for p, a in zip(problems, alpha))
+    return {"bound": "hbm", "achieved": b_alg[dom] / t_dom / 1e9, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": b_alg[dom] / t_dom / hbm, "traffic": None,
+            "kernel": "bat_stream (batched step kernel, rows over 128 variables)" if dom == "stream"
+                      else "bat_step (batched step kernel, rows up to 128 variables)",
+            "kernel_ms_per_launch": ms[dom],
+            "bytes_per_update_algorithmic": b_alg[dom] / (stream_upd if dom == "stream" else step_upd),
+            "achieved_compulsory_gbs": b_cmp[dom] / t_dom / 1e9,
+            "frac_compulsory": b_cmp[dom] / t_dom / hbm,
+            "kernels_ms_per_generation": ms,
+            "generation_ms": gen_s * 1e3,
+            "generation_frac": t_all / gen_s, "generation_frac_compulsory": t_all_c / gen_s,
+            "generation_frac_sum_of_instance_max": t_sum_max / gen_s,
+            "alpha_mean": float(sum(alpha) / len(alpha)),
+            "peak_note": f"HBM copy bandwidth {which}; achieved counts 6 + 4 alpha "
+                         "algorithmic bytes per update of the kernel's rows (alpha measured per "
+                         "instance); the generation fractions bound the whole step"}
+
+
+def fitness_error(psso, h, problems, prec, sample=64, seed=7):
+    """Relative error of the FP32 fitness against FP64 on the final state of
+    a run: the stored pBest values (what the run keeps and reports) and a raw
+    FP32 evaluation of the same rows, on the gBest and `sample` random
+    particles of each instance.  The FP64 values come from psso_evaluate in
+    FP64 (the oracle's summation order)."""
+    import numpy as np
+    if prec != "f32":
+        return None
+    rng = np.random.default_rng(seed)
+    stored, raw = [], []
+    for k, p in enumerate(problems[:8]):
+        N, D = p["N"], p["D"]
+        X, P, pF = psso.psso_get_state(h, k, N, D)
+        _, b, _ = psso.psso_best(h, k)
+        idx = np.unique(np.concatenate([[b], rng.choice(N, size=min(sample, N), replace=False)]))
+        rows = P[idx]
+        f64, _ = psso.psso_evaluate(p["fn"], rows, p["o"], p["w"], p["M"], precision="f64")
+        f32, _ = psso.psso_evaluate(p["fn"], rows, p["o"], p["w"], p["M"], precision="f32")
+        floor = 1e-6 * (20 + np.e) if p["fn"].endswith("ackley") else 0.0
+        scale = np.maximum(np.abs(f64), floor)
+        scale = np.where(scale > 0, scale, 1.0)
+        stored.append(np.abs(pF[idx] - f64) / scale)
+        raw.append(np.abs(f32 - f64) / scale)
+    stored, raw = np.concatenate(stored), np.concatenate(raw)
+    return {"pbest_rel_max": float(stored.max()), "pbest_rel_median": float(np.median(stored)),
+            "eval_rel_max": float(raw.max()), "eval_rel_median": float(np.median(raw)),
+            "rows": int(stored.size), "target": 1e-6,
+            "note": "relative to max(|f64|, 1e-6 (20 + e)) for Ackley, |f64| otherwise"}
 
 
 def psso_best_values(psso, problems, prec, t, sptr):
@@ -382,6 +559,10 @@ def grad_arm(psso, torch, problems, stream, flush, reps=20):
     return out
 
 
+def sptr_of(torch):
+    return torch.cuda.current_stream().cuda_stream
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -402,6 +583,7 @@ def main():
     import paper_2110_01470_gb300 as psso
     import workload
 
+    live = psso.psso_microbench(sptr_of(torch))   # measured pipe / latency peaks of this GPU
     cfg = workload.config(args.workload)
     t = args.generations or cfg["t"]
     problems = replica_problems(cfg["problems"], rank)
@@ -458,6 +640,7 @@ def main():
     st_end = psso.psso_stats(h)
     rechecks, refinements = st_end["rechecks"], st_end["refinements"]
     best = psso.psso_best(h, 0)
+    fit_err = fitness_error(psso, h, problems, prec)
     psso.psso_destroy(h)
     total = sum(step_ms)
     total = max_over_ranks(total, dist, "cuda")
@@ -506,20 +689,24 @@ def main():
 
     # --- roofline of the dominant kernel ------------------------------------------------------
     p0 = problems[0]
-    tensor = tensor_roofline(psso, problems, prec, sptr)
-    ops = sum(alu_ops_per_update(p) * p["N"] * p["D"] * t for p in problems)
     kernel_s = (sum(kern_ms) / len(kern_ms)) / 1e3
-    peak = SM_COUNT * LANES_PER_SM * ALU_CLOCK_MHZ * 1e6 / 1e12     # T ops / s
-    achieved = ops / kernel_s / 1e12
-    traffic = (GEN_TRAFFIC_BYTES.get((p0["fn"], p0["N"], p0["D"], t, prec))
-               if len(problems) == 1 else None)
-    roofline = tensor or {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "sso_generations<float, true>" if prec == "f32" else
-                          "sso_generations<..., false>",
-                "ops_per_update": ops / upd_per_step,
-                "kernel_ms_per_launch": kernel_s * 1e3,
-                "peak_note": "152 SMs x 128 lanes x 2070 MHz (derived, not measured)"}
+    n_bat = st.get("batch_classes", 0)
+    if n_bat and st["blocks"] == 0:
+        roofline = batched_roofline(psso, problems, prec, t, sptr, live)
+    else:
+        roofline = tensor_roofline(psso, problems, prec, sptr, args.workload)
+    if roofline is None:
+        per_lane = -(-(-(-p0["D"] // 4)) // 32)          # chunks of 4 variables per lane
+        width = 1 if per_lane <= 1 else 2 if per_lane <= 2 else 4 if per_lane <= 4 else 8
+        name = (f"sso_generations<{'float' if p0['lattice'] == 'f32' else 'double'}, "
+                f"F32R={1 if prec == 'f32' else 0}, MC={width}>")
+        roofline = alu_roofline(problems, t, prec, kernel_s, live, name)
+        roofline["traffic"] = (traffic_of("sso_generations", args.workload)
+                               if len(problems) == 1 else None)
+        # the sequential generations also bound the run from below by latency:
+        # at least one store -> polled-load hand-off per generation across blocks
+        roofline["latency_floor_ms"] = t * live["l2_handoff_ns"] * 1e-6 if st["blocks"] > 1 else None
+        roofline["us_per_generation"] = kernel_s * 1e6 / t
 
     if rank != 0:
         if dist:
@@ -546,6 +733,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roofline,
+        "fitness_err_vs_fp64": fit_err,
+        "peaks": live,
         "clocks": clk.summary(),
     }
     if polish is not None:

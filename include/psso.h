@@ -164,8 +164,23 @@ typedef struct {
     int32_t batch_blocks_per_sm;/* batched pipeline: resident blocks per SM of each
                                    step kernel's grid (0 = the occupancy maximum;
                                    larger values are clamped to it)                 */
-    int32_t reserved;           /* must be 0                                        */
+    int32_t flow;               /* psso_flow: 0 = synchronous generations (Alg. 2),
+                                   1 = asynchronous generations (Alg. 1)           */
 } psso_config;
+
+/* Generation flow (psso_config.flow).
+ *   SYNC   Alg. 2, the PSSO flow: every particle searches with the gBest of the
+ *          previous generation; pBest_i <- x_i when f <= pF (Alg. 3); gBest is
+ *          then the lowest-index arg-min of the pBest fitness (Alg. 4).
+ *   ASYNC  Alg. 1, the sequential CPU-SSO: particles are taken in index order;
+ *          particle i searches with the gBest left by particles 0..i-1 of the
+ *          same generation, replaces its pBest when f < pF and the gBest when
+ *          f < gF (both strict, as Alg. 1 writes them).  Runs as rounds of
+ *          speculative search of all remaining particles and ordered commit up
+ *          to the first one that beats the gBest.  One instance per handle,
+ *          PSSO_PREC_F64 only (else PSSO_ERR_UNSUPPORTED); results are
+ *          bit-identical to the CPU oracle's Alg. 1. */
+typedef enum { PSSO_FLOW_SYNC = 0, PSSO_FLOW_ASYNC = 1 } psso_flow;
 
 /* One log entry (psso_get_log). */
 typedef struct {
@@ -369,7 +384,11 @@ psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift
  * kernel's mean duration in ms to ms[0..10] (update, GEMM + fitness epilogue,
  * decisions, FP32 refinement rotation and decisions, FP64 rotation and
  * decisions, arg-min, FP64 rotation and decisions of arg-min candidates,
- * gBest); n >= 11.  The paper has no counterpart.  Synchronises.
+ * gBest); n >= 11.  On a handle whose swarms all run on the batched
+ * pipeline it times that pipeline instead, writing the mean per-generation
+ * duration of its streaming step kernels (rows over 128 variables), of its
+ * other step kernels and of its arg-min kernel to ms[0..2] (n >= 3; instance
+ * is ignored).  The paper has no counterpart.  Synchronises.
  * PSSO_ERR_UNSUPPORTED for a swarm on the persistent kernel. */
 psso_status psso_time_kernels(psso_handle h, int32_t instance, int32_t generations, float* ms, int32_t n);
 
@@ -402,6 +421,30 @@ typedef struct {
  * Allocates and frees device memory for each candidate; synchronises. */
 psso_status psso_autotune(const psso_problem* problems, int32_t count, const psso_config* cfg,
                           int32_t generations, psso_config* tuned, psso_tune_report* report);
+
+/* Measured peaks of this GPU (psso_microbench); the paper has no counterpart.
+ * Rates are operations per second over the whole GPU; latencies in ns. */
+typedef struct {
+    double fp32_fma_per_s;       /* FP32 fused multiply-adds                           */
+    double fp64_fma_per_s;       /* FP64 fused multiply-adds                           */
+    double int_mad_per_s;        /* 32-bit integer multiply-adds (low half)            */
+    double int_mulhi_xor_per_s;  /* pairs (high half of a 32 x 32 product, xor)        */
+    double philox_blocks_per_s;  /* Philox-4x32-10 blocks (the update's draws)          */
+    double l2_handoff_ns;        /* a store on one SM seen by a polling load on another */
+    double grid_barrier_ns;      /* a grid barrier of one block per SM (counter + flag) */
+    double cluster_barrier_ns;   /* a hardware barrier of an 8-CTA cluster              */
+    double sm_clock_mhz;         /* SM clock during the FP32 kernel (clock64 / timer)   */
+    int32_t sms;                 /* streaming multiprocessors                           */
+    int32_t reserved;
+} psso_peaks;
+
+/* Runs the microbenchmarks behind psso_peaks on the current device and
+ * `stream` (cudaStream_t, NULL = default): independent dependency chains of
+ * each operation on every SM, timed with CUDA events after a warm-up launch,
+ * and cooperative latency kernels whose waits are bounded (PSSO_ERR_TIMEOUT
+ * if one ran out).  Takes well under a second; allocates 4 KiB for the call;
+ * synchronises.  Changes no device setting. */
+psso_status psso_microbench(psso_peaks* out, void* stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);

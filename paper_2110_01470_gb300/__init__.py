@@ -32,6 +32,7 @@ PSSO_SPHERE, PSSO_ELLIPSOID, PSSO_RASTRIGIN, PSSO_ROSENBROCK, PSSO_ACKLEY, \
 PSSO_LATTICE_F64, PSSO_LATTICE_F32 = 0, 1
 PSSO_PREC_F64, PSSO_PREC_F32_RECHECK = 0, 1
 PSSO_ORDER_GPX, PSSO_ORDER_PAPER = 0, 1
+PSSO_FLOW_SYNC, PSSO_FLOW_ASYNC = 0, 1
 
 FN = {"sphere": PSSO_SPHERE, "ellipsoid": PSSO_ELLIPSOID, "rastrigin": PSSO_RASTRIGIN,
       "rosenbrock": PSSO_ROSENBROCK, "ackley": PSSO_ACKLEY, "rot_ellipsoid": PSSO_ROT_ELLIPSOID,
@@ -67,13 +68,22 @@ class psso_config(ctypes.Structure):
                 ("fault_skip_rank", ctypes.c_int32), ("residency", ctypes.c_int32),
                 ("pipeline", ctypes.c_int32), ("tensor_rotation", ctypes.c_int32),
                 ("batch_stream", ctypes.c_int32), ("batch_blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flow", ctypes.c_int32)]
 
 
 class psso_tune_report(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("batch_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
+class psso_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+                ("int_mad_per_s", ctypes.c_double), ("int_mulhi_xor_per_s", ctypes.c_double),
+                ("philox_blocks_per_s", ctypes.c_double), ("l2_handoff_ns", ctypes.c_double),
+                ("grid_barrier_ns", ctypes.c_double), ("cluster_barrier_ns", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class psso_log_entry(ctypes.Structure):
@@ -145,6 +155,7 @@ def load(path: str = LIB_PATH):
         "psso_autotune": ([ctypes.POINTER(psso_problem), ctypes.c_int32,
                            ctypes.POINTER(psso_config), ctypes.c_int32,
                            ctypes.POINTER(psso_config), ctypes.POINTER(psso_tune_report)], st),
+        "psso_microbench": ([ctypes.POINTER(psso_peaks), ctypes.c_void_p], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -183,7 +194,8 @@ def psso_create(fn, N, D, lb, ub, Cg, Cp, Cw, seed):
 
 _CONFIG_KEYS = ("threads_per_block", "single_block_max", "log_stride", "log_capacity",
                 "spin_limit", "stream", "max_blocks", "fault_skip_rank", "residency", "pipeline",
-                "tensor_rotation", "batch_stream", "batch_blocks_per_sm")
+                "tensor_rotation", "batch_stream", "batch_blocks_per_sm", "flow")
+FLOW = {"sync": PSSO_FLOW_SYNC, "async": PSSO_FLOW_ASYNC}
 
 
 def _config(precision, opts):
@@ -195,6 +207,8 @@ def _config(precision, opts):
     cfg = psso_config()
     cfg.precision = int(precision)
     for k, v in opts.items():
+        if k == "flow" and isinstance(v, str):
+            v = FLOW[v]
         setattr(cfg, k, v)
     return cfg
 
@@ -391,12 +405,31 @@ def psso_time_kernels(h, instance=0, generations=10):
     return dict(zip(PIPELINE_KERNELS, list(ms)[:len(PIPELINE_KERNELS)]))
 
 
+BATCH_KERNELS = ("stream", "step", "argmin")
+
+
+def psso_time_batch_kernels(h, generations=10):
+    """psso_time_kernels on a handle that runs the batched pipeline: mean ms
+    per generation of its streaming step kernels, other step kernels and
+    arg-min kernel."""
+    ms = (ctypes.c_float * 16)()
+    _check(load().psso_time_kernels(h, 0, int(generations), ctypes.addressof(ms), 16))
+    return dict(zip(BATCH_KERNELS, list(ms)[:3]))
+
+
 def psso_polish(h, instance=0, steps=20, lr=1e-3):
     """Gradient polish of the gBest row of ``instance``; returns True when it
     replaced the gBest particle's pBest (strictly lower FP64 fitness)."""
     improved = ctypes.c_int32(0)
     _check(load().psso_polish(h, int(instance), int(steps), float(lr), ctypes.byref(improved)))
     return bool(improved.value)
+
+
+def psso_microbench(stream=None):
+    """Measured peaks of the current GPU (dict of psso_peaks fields)."""
+    out = psso_peaks()
+    _check(load().psso_microbench(ctypes.byref(out), stream))
+    return {k: getattr(out, k) for k, _ in psso_peaks._fields_ if k != "reserved"}
 
 
 def psso_last_error():

@@ -127,6 +127,13 @@ struct psso_ctx {
     int64_t h2d = 0, d2h = 0;
     int64_t launches = 0;       // kernels this handle enqueued (graph nodes included)
     bool failed = false;
+    // asynchronous flow (Alg. 1): one cooperative kernel; its scratch and control words
+    bool async = false;
+    void* amem = nullptr;
+    AsyncCtl* actl = nullptr;
+    void* axs = nullptr;
+    double* afs = nullptr;
+    int agrid = 0, ablock = 256;
 };
 
 namespace {
@@ -212,7 +219,8 @@ psso_status plan(psso_ctx* h)
         total_cost += (double)I.pr.N * I.Dp;
         h->mc_index = std::max(h->mc_index, I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0);
     }
-    if (n_kernel == 0) {                    // every instance runs on the tensor-core pipeline
+    if (n_kernel == 0 || h->async) {        // every instance runs on the tensor-core pipeline,
+                                            // or the handle runs the asynchronous flow
         h->grid = 0;
         h->units.clear();
         h->block_first.assign(1, 0);
@@ -443,6 +451,22 @@ void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
 
 psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
 {
+    if (h->async) {
+        const HostInst& I = h->inst[0];
+        AsyncParams a{};
+        a.inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
+        a.status = reinterpret_cast<StatusDev*>(h->arena + h->off_status);
+        a.ctl = h->actl;
+        a.xs = h->axs;
+        a.fs = h->afs;
+        a.g_begin = g_begin;
+        a.g_end = g_end;
+        a.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : (int64_t)50000000;
+        const int mc = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
+        CUDA_TRY(async_call((int)h->pos_size, mc, 0, &a, h->agrid, h->ablock, h->stream, nullptr));
+        ++h->launches;
+        return PSSO_OK;
+    }
     KParams p{};
     p.inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
     p.units = reinterpret_cast<const UnitDev*>(h->arena + h->off_units);
@@ -543,16 +567,24 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     return PSSO_OK;
 }
 
-cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s)
+// With ev (classes + 2 events), an event is recorded before the first kernel
+// and after each kernel (one step kernel per class, then the arg-min).
+cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s, cudaEvent_t* ev = nullptr)
 {
     const InstDev* inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
+    int q = 0;
+    if (ev) cudaEventRecord(ev[q++], s);
     for (const auto& c : h->bat.classes) {
         BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, h->bat.gen, h->bat.cnt};
         const cudaError_t e = c.stream ? bat_call(h->variant, 3, 2, &p, c.grid, 256, s, nullptr)
                                        : bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
         if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[q++], s);
     }
-    return launch_bat_argmin(h->variant, inst, h->bat.all_ids, h->bat.n_all, h->bat.gen, h->bat.cnt, s);
+    const cudaError_t e =
+        launch_bat_argmin(h->variant, inst, h->bat.all_ids, h->bat.n_all, h->bat.gen, h->bat.cnt, s);
+    if (ev) cudaEventRecord(ev[q++], s);
+    return e;
 }
 
 // Classes of equal (lane-group width, chunks per lane), their device tables,
@@ -648,6 +680,36 @@ psso_status setup_bat(psso_ctx* h)
     return PSSO_OK;
 }
 
+// The asynchronous flow's scratch (searched rows and their fitness) and
+// control words, and its grid: co-resident blocks, no more than the
+// particles need.
+psso_status setup_async(psso_ctx* h)
+{
+    if (!h->async) return PSSO_OK;
+    const HostInst& I = h->inst[0];
+    const size_t N = (size_t)I.pr.N, row = (size_t)I.Dp * h->pos_size;
+    const size_t ctl = align_up(sizeof(AsyncCtl), 256), xs = align_up(N * row, 256);
+    cudaError_t e = cudaMalloc(&h->amem, ctl + xs + N * 8);
+    if (e != cudaSuccess) {
+        h->amem = nullptr;
+        return fail(PSSO_ERR_OOM, std::string("cudaMalloc of the asynchronous flow's scratch: ") +
+                                      cudaGetErrorString(e));
+    }
+    h->actl = static_cast<AsyncCtl*>(h->amem);
+    h->axs = static_cast<char*>(h->amem) + ctl;
+    h->afs = reinterpret_cast<double*>(static_cast<char*>(h->amem) + ctl + xs);
+    CUDA_TRY(cudaMemsetAsync(h->amem, 0, ctl, h->stream));
+    const int mc = I.maxc >= 8 ? 3 : I.maxc >= 4 ? 2 : I.maxc >= 2 ? 1 : 0;
+    int per_sm = 0, sms = 0;
+    CUDA_TRY(async_call((int)h->pos_size, mc, 1, nullptr, 0, h->ablock, nullptr, &per_sm));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (per_sm < 1) return fail(PSSO_ERR_UNSUPPORTED, "the asynchronous kernel does not fit an SM");
+    const int64_t groups_per_block = (int64_t)(h->ablock / 32) * (32 / I.G);
+    const int64_t need = ((int64_t)I.pr.N + groups_per_block - 1) / groups_per_block;
+    h->agrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, need));
+    return PSSO_OK;
+}
+
 psso_status read_status(psso_ctx* h)
 {
     CUDA_TRY(cudaSetDevice(h->device));
@@ -702,7 +764,9 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     if (c.batch_stream < -1 || c.batch_stream > 1) return fail(PSSO_ERR_ARG, "batch_stream must be -1, 0 or 1");
     if (c.batch_blocks_per_sm < 0 || c.batch_blocks_per_sm > 64)
         return fail(PSSO_ERR_ARG, "batch_blocks_per_sm must be in [0, 64]");
-    if (c.reserved != 0) return fail(PSSO_ERR_ARG, "psso_config.reserved must be 0");
+    if (c.flow != PSSO_FLOW_SYNC && c.flow != PSSO_FLOW_ASYNC) return fail(PSSO_ERR_ARG, "unknown flow");
+    if (c.flow == PSSO_FLOW_ASYNC && (count != 1 || c.precision != PSSO_PREC_F64))
+        return fail(PSSO_ERR_UNSUPPORTED, "the asynchronous flow runs one instance with PSSO_PREC_F64");
     for (int32_t k = 0; k < count; ++k) {
         psso_status st = check_problem(problems[k], c.precision, k);
         if (st != PSSO_OK) return st;
@@ -719,6 +783,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     h->pos_size = h->lattice == PSSO_LATTICE_F32 ? 4 : 8;
     h->block = c.threads_per_block ? c.threads_per_block : 256;
     h->stream = static_cast<cudaStream_t>(c.stream);
+    h->async = c.flow == PSSO_FLOW_ASYNC;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
         return fail(PSSO_ERR_CUDA, "no CUDA device");
@@ -738,7 +803,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     {
         int n_plain = 0;
         for (const auto& I : h->inst) n_plain += I.tc ? 0 : 1;
-        const bool bat = c.batch_stream == 1 || (c.batch_stream == 0 && n_plain >= 16);
+        const bool bat = !h->async && (c.batch_stream == 1 || (c.batch_stream == 0 && n_plain >= 16));
         for (auto& I : h->inst) I.bp = bat && !I.tc;
     }
     psso_status st = plan(h);
@@ -864,6 +929,8 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     }
     st = setup_bat(h);
     if (st != PSSO_OK) return cleanup_fail(st);
+    st = setup_async(h);
+    if (st != PSSO_OK) return cleanup_fail(st);
     st = launch(h, 0, 0);
     if (st != PSSO_OK) return cleanup_fail(st);
     for (auto& I : h->inst) h->evals += I.pr.N;
@@ -929,6 +996,7 @@ psso_status psso_reset(psso_handle h)
     CUDA_TRY(cudaMemsetAsync(h->arena + h->off_status, 0, sizeof(StatusDev), h->stream));
     for (auto& I : h->inst)
         if (I.tc) CUDA_TRY(cudaMemsetAsync(&I.rh.dev.ctl->status, 0, sizeof(int), h->stream));
+    if (h->actl) CUDA_TRY(cudaMemsetAsync(h->actl, 0, sizeof(AsyncCtl), h->stream));
     psso_status st = launch(h, 0, 0);
     if (st != PSSO_OK) return st;
     h->gen = 0;
@@ -1039,8 +1107,8 @@ psso_status psso_stats(psso_handle h, psso_stats_t* out)
     out->generations = h->gen;
     out->evaluations = h->evals;
     out->updates = h->updates;
-    out->blocks = h->grid;
-    out->threads_per_block = h->block;
+    out->blocks = h->async ? h->agrid : h->grid;
+    out->threads_per_block = h->async ? h->ablock : h->block;
     out->instances = (int32_t)h->inst.size();
     out->batch_classes = (int32_t)h->bat.classes.size();
     int64_t r = 0;
@@ -1090,12 +1158,49 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
     return PSSO_OK;
 }
 
+// Batched pipeline: per generation, the streaming step kernels (rows over 128
+// variables), the narrow-row step kernels, and the arg-min kernel.
+static psso_status time_bat_kernels(psso_ctx* h, int32_t generations, float* ms, int32_t n)
+{
+    if (n < 3) return fail(PSSO_ERR_ARG, "psso_time_kernels needs room for 3 values on a batched handle");
+    if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier");
+    if (h->gen + generations > 0xfffffff0LL) return fail(PSSO_ERR_ARG, "generation counter would exceed 2^32");
+    CUDA_TRY(cudaSetDevice(h->device));
+    const int K = (int)h->bat.classes.size() + 1;
+    std::vector<cudaEvent_t> ev(K + 1);
+    for (auto& x : ev) CUDA_TRY(cudaEventCreate(&x));
+    double acc[3] = {0.0, 0.0, 0.0};
+    cudaError_t e = launch_bat_set_gen(h->bat.gen, h->gen + 1, h->stream);
+    for (int32_t g = 0; g < generations && e == cudaSuccess; ++g) {
+        e = enqueue_bat_generation(h, h->stream, ev.data());
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
+        for (int q = 0; q < K && e == cudaSuccess; ++q) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+            const int slot = q + 1 == K ? 2 : (h->bat.classes[q].stream ? 0 : 1);
+            acc[slot] += t;
+        }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(PSSO_ERR_CUDA, std::string("psso_time_kernels: ") + cudaGetErrorString(e));
+    h->gen += generations;
+    for (const auto& I : h->inst) {
+        h->evals += I.pr.N * generations;
+        h->updates += I.pr.N * I.pr.D * generations;
+    }
+    h->launches += 1 + (int64_t)K * generations;
+    for (int q = 0; q < n; ++q) ms[q] = q < 3 ? (float)(acc[q] / generations) : 0.f;
+    return PSSO_OK;
+}
+
 psso_status psso_time_kernels(psso_handle h, int32_t instance, int32_t generations, float* ms, int32_t n)
 {
     if (!h || !ms) return fail(PSSO_ERR_ARG, "handle or ms is NULL");
     if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
     if (generations < 1 || n < rot::KERNELS_PER_GENERATION)
         return fail(PSSO_ERR_ARG, "need generations >= 1 and room for every kernel of a generation");
+    if (h->bat.n_all > 0 && h->bat.n_all == (int32_t)h->inst.size())
+        return time_bat_kernels(h, generations, ms, n);
     if (h->inst.size() != 1) return fail(PSSO_ERR_ARG, "psso_time_kernels needs a single-instance handle");
     HostInst& I = h->inst[instance];
     if (!I.tc) return fail(PSSO_ERR_UNSUPPORTED, "the instance runs on the persistent kernel (one launch per run)");
@@ -1176,6 +1281,7 @@ psso_status psso_load(psso_handle h, const void* buf, size_t n)
     CUDA_TRY(cudaMemset(h->arena + h->off_status, 0, sizeof(StatusDev)));
     for (auto& I : h->inst)
         if (I.tc) CUDA_TRY(cudaMemset(&I.rh.dev.ctl->status, 0, sizeof(int)));
+    if (h->actl) CUDA_TRY(cudaMemset(h->actl, 0, sizeof(AsyncCtl)));
     h->gen = hd.gen;
     h->evals = hd.evals;
     h->updates = hd.updates;
@@ -1198,6 +1304,7 @@ void psso_destroy(psso_handle h)
     if (h->bat.graph1) cudaGraphExecDestroy(h->bat.graph1);
     if (h->bat.graphG) cudaGraphExecDestroy(h->bat.graphG);
     if (h->bat.mem) cudaFree(h->bat.mem);
+    if (h->amem) cudaFree(h->amem);
     delete h;
 }
 

@@ -179,6 +179,26 @@ cudaError_t launch_bat_argmin(int variant, const InstDev* inst, const int32_t* i
                               BatCounters* cnt, cudaStream_t s);
 cudaError_t launch_bat_set_gen(long long* gen, long long g, cudaStream_t s);
 
+// Asynchronous flow (Alg. 1): control words of the grid barrier and of the
+// rounds of speculation and ordered commit (async_kernel.cu).
+struct AsyncCtl {
+    unsigned bar_count, bar_gen;   // grid barrier: arrivals, generation word
+    unsigned first[3];             // lowest improving particle of a round (3 rotating slots)
+    unsigned pad;
+    unsigned long long acc[2];     // pBest updates of a generation (by parity)
+};
+struct AsyncParams {
+    const InstDev* inst;
+    StatusDev* status;
+    AsyncCtl* ctl;
+    void* xs;                      // [N][Dp] searched positions of the current round
+    double* fs;                    // [N] their FP64 fitness
+    int64_t g_begin, g_end, spin_limit;
+};
+// op 0: launch (cooperative) over grid x block; op 1: occupancy (blocks per SM).
+cudaError_t async_call(int pos_size, int mc_index, int op, const AsyncParams* p, int grid, int block,
+                       cudaStream_t s, int* out);
+
 cudaError_t launch_polish(const InstDev* inst, int k, int lattice, int owner_rank, int64_t g, int steps,
                           float lr, cudaStream_t s);
 

@@ -75,7 +75,7 @@ def test_binding_structs_match_header(tmp_path):
     import paper_2110_01470_gb300 as psso
     structs = {"psso_problem": psso.psso_problem, "psso_config": psso.psso_config,
                "psso_log_entry": psso.psso_log_entry, "psso_stats_t": psso.psso_stats_t,
-               "psso_tune_report": psso.psso_tune_report}
+               "psso_tune_report": psso.psso_tune_report, "psso_peaks": psso.psso_peaks}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "psso.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
@@ -99,7 +99,7 @@ def test_binding_config_fields():
     import paper_2110_01470_gb300 as psso
     cfg = psso._config("f32", {"batch_blocks_per_sm": 3, "threads_per_block": 384, "log_stride": 1})
     assert (cfg.precision, cfg.batch_blocks_per_sm, cfg.threads_per_block, cfg.log_stride) == (1, 3, 384, 1)
-    assert cfg.reserved == 0 and cfg.stream is None
+    assert cfg.flow == 0 and cfg.stream is None
     with pytest.raises(TypeError):
         psso._config("f64", {"threads": 64})
 
