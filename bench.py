@@ -385,6 +385,7 @@ def batched_roofline(psso, problems, prec, t, sptr, live, gens=20):
     HBM and all operations / the measured ALU rate (instances run
     concurrently, so their times do not add)."""
     alpha = accept_rate(psso, problems, prec, t, sptr)
+    peaks, which = measured_peaks()
     h = psso.psso_create_ex(problems, prec, stream=sptr)
     try:
         psso.psso_run(h, 3)
@@ -409,7 +410,6 @@ def batched_roofline(psso, problems, prec, t, sptr, live, gens=20):
     ops_all = sum(alu_ops_per_update(p, prec) * p["N"] * p["D"] for p in problems)
     alu = alu_roofline(problems, 1, prec, 1.0, live, "")
     alu_rate = alu["peak"] * 1e12
-    peaks, which = measured_peaks()
     gen_s = (ms["stream"] + ms["step"] + ms["argmin"]) / 1e3
     t_all = max((b_alg["stream"] + b_alg["step"]) / hbm, ops_all / alu_rate)
     t_all_c = max((b_cmp["stream"] + b_cmp["step"]) / hbm, ops_all / alu_rate)

@@ -65,13 +65,25 @@ typedef enum {
 } psso_status;
 
 /* Test functions (Table 3.2 of the paper; shifted by o, rotated by M).
- * z = x - o (or z = M (x - o) for the rotated forms):
- *   SPHERE        sum z_j^2
- *   ELLIPSOID     sum w_j z_j^2            (w given, e.g. 10^(6j/(D-1)))
- *   RASTRIGIN     10 D + sum (z_j^2 - 10 cos(2 pi z_j))
- *   ROSENBROCK    sum_{j<D-1} 100 (a_{j+1} - a_j^2)^2 + (a_j - 1)^2,  a = z + 1
- *   ACKLEY        -20 exp(-0.2 sqrt(sum z^2 / D)) - exp(sum cos(2 pi z) / D) + 20 + e
- * Every function is 0 at x = o. */
+ * z = x - o (or z = M (x - o) for the rotated forms), j = 0 .. D-1:
+ *   SPHERE           sum z_j^2                                         (f1)
+ *   ELLIPSOID        sum w_j z_j^2            (w given, e.g. 10^(6j/(D-1)))
+ *   RASTRIGIN        10 D + sum (z_j^2 - 10 cos(2 pi z_j))              (f5)
+ *   ROSENBROCK       sum_{j<D-1} 100 (a_{j+1} - a_j^2)^2 + (a_j - 1)^2,
+ *                    a = z + 1                                         (f4)
+ *   ACKLEY           -20 exp(-0.2 sqrt(sum z^2 / D)) - exp(sum cos(2 pi z) / D)
+ *                    + 20 + e                                          (f6)
+ *   HYPER_ELLIPSOID  sum (j + 1) z_j^2 (ELLIPSOID with w_j = j + 1)    (f2)
+ *   SCHWEFEL12       sum_i (sum_{j<=i} z_j)^2                          (f3)
+ *   GRIEWANK         1 + sum z_j^2 / 4000 - prod cos(z_j / sqrt(j + 1)) (f7)
+ *   POWELL           sum over blocks of 4 variables of (z0 + 10 z1)^2 +
+ *                    5 (z2 - z3)^2 + (z1 - 2 z2)^4 + 10 (z0 - z3)^4, with
+ *                    z = 0 beyond D                                    (f8)
+ *   SCHWEFEL         418.9829 D - sum z_j sin(sqrt|z_j|)                (f9)
+ * Every function but SCHWEFEL is 0 at x = o (SCHWEFEL is near its minimum,
+ * about 1.3e-5 D, at z_j = 420.9687).  SCHWEFEL12, GRIEWANK, POWELL and
+ * SCHWEFEL have FP64 fitness only: PSSO_PREC_F32_RECHECK and the FP32
+ * gradient calls return PSSO_ERR_UNSUPPORTED for them. */
 typedef enum {
     PSSO_SPHERE = 0,
     PSSO_ELLIPSOID = 1,
@@ -80,7 +92,12 @@ typedef enum {
     PSSO_ACKLEY = 4,
     PSSO_ROT_ELLIPSOID = 5,
     PSSO_ROT_RASTRIGIN = 6,
-    PSSO_ROT_ACKLEY = 7
+    PSSO_ROT_ACKLEY = 7,
+    PSSO_HYPER_ELLIPSOID = 8,
+    PSSO_SCHWEFEL12 = 9,
+    PSSO_GRIEWANK = 10,
+    PSSO_POWELL = 11,
+    PSSO_SCHWEFEL = 12
 } psso_fn;
 
 /* Position lattice: which grid fresh values (Eq. 2.1's last branch and the
@@ -123,7 +140,7 @@ typedef struct {
     uint32_t stream_id;  /* Philox counter stream, < 2^24 (independent instances)   */
     uint32_t order;      /* psso_order (0 = GPX)                                    */
     const double* shift;    /* host, D values, or NULL for o = 0                    */
-    const double* weights;  /* host, D values; required by the ellipsoid functions  */
+    const double* weights;  /* host, D values; required by ELLIPSOID, ROT_ELLIPSOID  */
     const double* rotation; /* host, D*D row-major M; required by rotated functions */
 } psso_problem;
 

@@ -48,6 +48,11 @@ FN = {
     "rot_ellipsoid": 5,
     "rot_rastrigin": 6,
     "rot_ackley": 7,
+    "hyper_ellipsoid": 8,
+    "schwefel12": 9,
+    "griewank": 10,
+    "powell": 11,
+    "schwefel": 12,
 }
 LATTICE = {"f64": 0, "f32": 1}
 TAG_INIT, TAG_RHO, TAG_FRESH = 1, 2, 3

@@ -50,6 +50,18 @@
  *     identity); Ackley's exp(.)-exp(.)+20+e is evaluated through expm1 of the
  *     same arguments with cos(2 pi z) = 1 - 2 sin^2(pi z) (exact identities);
  *     Rosenbrock is shifted so that f(o) = 0 (z = x - o + 1).
+ *   * The rest of Table 3.2 (f2, f3, f7, f8, f9), shifted by o:
+ *       f2 hyper-ellipsoid  sum (j+1) z_j^2
+ *       f3 Schwefel's       sum_i (sum_{j<=i} z_j)^2 (Schwefel's problem 1.2; the
+ *                           printed inner sum of squares would make f3 a
+ *                           separable weighted sphere, which the paper's own
+ *                           classification of f3 as inseparable rules out)
+ *       f7 Griewank         1 + sum z_j^2 / 4000 - prod cos(z_j / sqrt(j+1))
+ *       f8 Powell           sum over blocks of 4: (z0 + 10 z1)^2 + 5 (z2 - z3)^2
+ *                           + (z1 - 2 z2)^4 + 10 (z0 - z3)^4, z = 0 beyond D
+ *                           (the printed form lacks the + between terms)
+ *       f9 Schwefel         418.9829 D - sum z_j sin(sqrt|z_j|)
+ *     with the fixed evaluation orders written out at each function.
  */
 #include <math.h>
 #include <stdint.h>
@@ -71,7 +83,12 @@ enum {
     FN_ROT_ELLIPSOID = 5,
     FN_ROT_RASTRIGIN = 6,
     FN_ROT_ACKLEY = 7,
-    FN_COUNT = 8
+    FN_HYPER_ELLIPSOID = 8,   /* Table 3.2 f2 */
+    FN_SCHWEFEL12 = 9,        /* Table 3.2 f3 */
+    FN_GRIEWANK = 10,         /* Table 3.2 f7 */
+    FN_POWELL = 11,           /* Table 3.2 f8 */
+    FN_SCHWEFEL = 12,         /* Table 3.2 f9 */
+    FN_COUNT = 13
 };
 
 enum { LATTICE_F64 = 0, LATTICE_F32 = 1 };
@@ -249,13 +266,86 @@ static double butterfly32(double v[32])
     return v[0];
 }
 
+static double butterfly32_mul(double v[32])
+{
+    for (int off = 16; off >= 1; off >>= 1) {
+        double t[32];
+        for (int l = 0; l < 32; ++l) t[l] = v[l] * v[l ^ off];
+        memcpy(v, t, sizeof t);
+    }
+    return v[0];
+}
+
+/* cos(a) = 1 - 2 sin^2(a / 2) with sin(a / 2) = sin(pi q), q = a * (1 / (2 pi))
+ * rounded once (INV_2PI the nearest double to 1 / (2 pi)); 1 - 2 s^2 as one
+ * fma.  Error against cos(a): about 2^-52 (1 + |a|). */
+static const double INV_2PI = 0x1.45f306dc9c883p-3;
+double oracle_sinpi(double x);
+static double cos_rad(double a)
+{
+    double s = oracle_sinpi(a * INV_2PI);
+    return fma(-2.0 * s, s, 1.0);
+}
+
+/* sin(a) = sin(pi q), q = a * (1 / pi) rounded once (INV_PI the nearest double
+ * to 1 / pi).  Error against sin(a): about 2^-52 (1 + |a|). */
+static const double INV_PI = 0x1.45f306dc9c883p-2;
+static double sin_rad(double a) { return oracle_sinpi(a * INV_PI); }
+
+/* Table 3.2 f3, read as Schwefel's problem 1.2: sum_i (sum_{j<=i} z_j)^2.  The
+ * prefix sums c_j follow a fixed blocked order over the 32-lane layout
+ * (variable block b = j>>2 of 4 variables on lane b&31, slice s = b>>5 of
+ * 128 variables):
+ *   block total   T_b = ((z_4b + z_4b+1) + z_4b+2) + z_4b+3   (z = 0 beyond D)
+ *   within slice  inclusive Kogge-Stone scan of the 32 block totals: for
+ *                 off = 1, 2, 4, 8, 16, v_l <- v_(l-off) + v_l for l >= off
+ *   slice carry   C_0 = 0, C_(s+1) = C_s + v_31 of slice s
+ *   block start   B_b = C_s + (l > 0 ? v_(l-1) : 0)
+ *   variables     c_4b = B_b + z_4b, c_(j+1) = c_j + z_(j+1) within the block
+ * and the terms c_j^2 are summed like every other function's terms (lane
+ * partials by fma in ascending j, then the butterfly). */
+static void schwefel12_prefix(int64_t D, const double* z, double* c)
+{
+    const int64_t nb = (D + 3) / 4, ns = (nb + 31) / 32;
+    double carry = 0.0;
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        double v[32], nv[32];
+        for (int l = 0; l < 32; ++l) {
+            const int64_t b = 32 * sl + l;
+            double t = 0.0;
+            for (int m = 0; m < 4; ++m) {
+                const int64_t j = 4 * b + m;
+                const double zj = (j < D) ? z[j] : 0.0;
+                t = (m == 0) ? zj : t + zj;
+            }
+            v[l] = (b < nb) ? t : 0.0;
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+            for (int l = 0; l < 32; ++l) nv[l] = (l >= off) ? v[l - off] + v[l] : v[l];
+            memcpy(v, nv, sizeof v);
+        }
+        for (int l = 0; l < 32; ++l) {
+            const int64_t b = 32 * sl + l;
+            if (b >= nb) break;
+            double run = carry + ((l > 0) ? v[l - 1] : 0.0);
+            for (int m = 0; m < 4; ++m) {
+                const int64_t j = 4 * b + m;
+                if (j >= D) break;
+                run = run + z[j];
+                c[j] = run;
+            }
+        }
+        carry = carry + v[31];
+    }
+}
+
 double oracle_fitness(int fn, int64_t D, const double* x, const double* o,
                       const double* w, const double* M)
 {
     double* z = (double*)malloc((size_t)D * sizeof(double));
     double* d = (double*)malloc((size_t)D * sizeof(double));
     double acc[32], acc2[32];
-    for (int l = 0; l < 32; ++l) { acc[l] = 0.0; acc2[l] = 0.0; }
+    for (int l = 0; l < 32; ++l) { acc[l] = 0.0; acc2[l] = 1.0; }
     for (int64_t j = 0; j < D; ++j) d[j] = x[j] - (o ? o[j] : 0.0);
     int rotated = (fn == FN_ROT_ELLIPSOID || fn == FN_ROT_RASTRIGIN || fn == FN_ROT_ACKLEY);
     if (rotated) {
@@ -273,6 +363,13 @@ double oracle_fitness(int fn, int64_t D, const double* x, const double* o,
     if (fn == FN_ROT_RASTRIGIN) base = FN_RASTRIGIN;
     if (fn == FN_ROT_ACKLEY) base = FN_ACKLEY;
 
+    double* c = NULL;
+    if (base == FN_SCHWEFEL12) {
+        c = (double*)malloc((size_t)D * sizeof(double));
+        schwefel12_prefix(D, z, c);
+    }
+    if (base == FN_ACKLEY)
+        for (int l = 0; l < 32; ++l) acc2[l] = 0.0;
     for (int64_t j = 0; j < D; ++j) {
         int l = (int)((j >> 2) & 31);
         double zj = z[j];
@@ -301,9 +398,41 @@ double oracle_fitness(int fn, int64_t D, const double* x, const double* o,
             acc2[l] = fma(s, s, acc2[l]);
             break;
         }
+        case FN_HYPER_ELLIPSOID:   /* f2: sum (j+1) z_j^2 */
+            acc[l] = fma((double)(j + 1), zj * zj, acc[l]);
+            break;
+        case FN_SCHWEFEL12:        /* f3: sum c_j^2, c the prefix sums of z */
+            acc[l] = fma(c[j], c[j], acc[l]);
+            break;
+        case FN_GRIEWANK:          /* f7: S = sum z^2 (divided by 4000 below), P = prod cos(z_j / sqrt(j+1)) */
+            acc[l] = fma(zj, zj, acc[l]);
+            acc2[l] = acc2[l] * cos_rad(zj / sqrt((double)(j + 1)));
+            break;
+        case FN_POWELL:            /* f8: one term per block of 4 variables (z = 0 beyond D) */
+            if ((j & 3) == 0) {
+                const double z0 = zj, z1 = (j + 1 < D) ? z[j + 1] : 0.0;
+                const double z2 = (j + 2 < D) ? z[j + 2] : 0.0, z3 = (j + 3 < D) ? z[j + 3] : 0.0;
+                const double a = fma(10.0, z1, z0), b = z2 - z3;
+                const double cc = fma(-2.0, z2, z1), dd = z0 - z3;
+                const double c2 = cc * cc, d2 = dd * dd;
+                /* (z0 + 10 z1)^2 + 5 (z2 - z3)^2 + (z1 - 2 z2)^4 + 10 (z0 - z3)^4 */
+                const double t = fma(a, a, fma(5.0 * b, b, fma(c2, c2, 10.0 * (d2 * d2))));
+                acc[l] = acc[l] + t;
+            }
+            break;
+        case FN_SCHWEFEL:          /* f9: S = sum z_j sin(sqrt|z_j|) */
+            acc[l] = fma(zj, sin_rad(sqrt(fabs(zj))), acc[l]);
+            break;
         }
     }
     double f = butterfly32(acc);
+    if (base == FN_GRIEWANK) {     /* 1 + S / 4000 - P, evaluated as (1 - P) + S / 4000 */
+        double P = butterfly32_mul(acc2);
+        f = (1.0 - P) + f / 4000.0;
+    }
+    if (base == FN_SCHWEFEL)       /* 418.9829 D - S */
+        f = 418.9829 * (double)D - f;
+    free(c);
     if (base == FN_ACKLEY) {
         /* -20 exp(-0.2 sqrt(S1/D)) - exp(sum cos(2 pi z)/D) + 20 + e
          *   = -20 expm1(-0.2 sqrt(S1/D)) - e expm1(-2 Q/D)              */

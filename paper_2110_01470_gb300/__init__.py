@@ -28,7 +28,8 @@ PSSO_OK, PSSO_ERR_ARG, PSSO_ERR_CUDA, PSSO_ERR_OOM, PSSO_ERR_TIMEOUT, PSSO_ERR_S
     PSSO_ERR_UNSUPPORTED = range(7)
 # psso_fn
 PSSO_SPHERE, PSSO_ELLIPSOID, PSSO_RASTRIGIN, PSSO_ROSENBROCK, PSSO_ACKLEY, \
-    PSSO_ROT_ELLIPSOID, PSSO_ROT_RASTRIGIN, PSSO_ROT_ACKLEY = range(8)
+    PSSO_ROT_ELLIPSOID, PSSO_ROT_RASTRIGIN, PSSO_ROT_ACKLEY, PSSO_HYPER_ELLIPSOID, \
+    PSSO_SCHWEFEL12, PSSO_GRIEWANK, PSSO_POWELL, PSSO_SCHWEFEL = range(13)
 PSSO_LATTICE_F64, PSSO_LATTICE_F32 = 0, 1
 PSSO_PREC_F64, PSSO_PREC_F32_RECHECK = 0, 1
 PSSO_ORDER_GPX, PSSO_ORDER_PAPER = 0, 1
@@ -36,7 +37,9 @@ PSSO_FLOW_SYNC, PSSO_FLOW_ASYNC = 0, 1
 
 FN = {"sphere": PSSO_SPHERE, "ellipsoid": PSSO_ELLIPSOID, "rastrigin": PSSO_RASTRIGIN,
       "rosenbrock": PSSO_ROSENBROCK, "ackley": PSSO_ACKLEY, "rot_ellipsoid": PSSO_ROT_ELLIPSOID,
-      "rot_rastrigin": PSSO_ROT_RASTRIGIN, "rot_ackley": PSSO_ROT_ACKLEY}
+      "rot_rastrigin": PSSO_ROT_RASTRIGIN, "rot_ackley": PSSO_ROT_ACKLEY,
+      "hyper_ellipsoid": PSSO_HYPER_ELLIPSOID, "schwefel12": PSSO_SCHWEFEL12,
+      "griewank": PSSO_GRIEWANK, "powell": PSSO_POWELL, "schwefel": PSSO_SCHWEFEL}
 LATTICE = {"f64": PSSO_LATTICE_F64, "f32": PSSO_LATTICE_F32}
 PRECISION = {"f64": PSSO_PREC_F64, "f32": PSSO_PREC_F32_RECHECK}
 ORDER = {"gpx": PSSO_ORDER_GPX, "paper": PSSO_ORDER_PAPER}

@@ -70,6 +70,30 @@ __device__ __forceinline__ double sinpi_sq_f64(double z)
     return __dmul_rn(s, s);
 }
 
+// sin(pi x) with its sign: x = n + r, n the nearest integer (half even),
+// sin(pi x) = (-1)^n sin(pi r); n is odd iff n / 2 is not an integer.
+__device__ __forceinline__ double sinpi_f64(double x)
+{
+    const double n = rint(x);
+    const double s = sinpi_reduced_f64(__dsub_rn(x, n));
+    const double h = __dmul_rn(n, 0.5);
+    return (h != rint(h)) ? -s : s;
+}
+
+// sin and cos of an argument in radians through sin(pi q), q = a / pi or
+// a / (2 pi) rounded once (the constants are the nearest doubles to 1 / pi and
+// 1 / (2 pi)); cos a = 1 - 2 sin^2(a / 2) as one fma.  Error about
+// 2^-52 (1 + |a|).
+__device__ __forceinline__ double sin_rad_f64(double a)
+{
+    return sinpi_f64(__dmul_rn(a, 0x1.45f306dc9c883p-2));
+}
+__device__ __forceinline__ double cos_rad_f64(double a)
+{
+    const double s = sinpi_f64(__dmul_rn(a, 0x1.45f306dc9c883p-3));
+    return __fma_rn(__dmul_rn(-2.0, s), s, 1.0);
+}
+
 __device__ __forceinline__ double expm1_series_f64(double x)
 {
     double p = 0x1.93974a8c07c9dp-37;          // 1/14!

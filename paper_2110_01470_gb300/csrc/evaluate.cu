@@ -65,15 +65,25 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
         set_last_error(msg);
         return st;
     };
-    if (!X || !f || N < 1 || D < 1 || D > 1024 || fn < PSSO_SPHERE || fn > PSSO_ROT_ACKLEY)
+    if (!X || !f || N < 1 || D < 1 || D > 1024 || fn < PSSO_SPHERE || fn > PSSO_SCHWEFEL)
         return bad(PSSO_ERR_ARG, "psso_evaluate: need X, f, N >= 1, 1 <= D <= 1024, a known function");
-    if (fn >= PSSO_ROT_ELLIPSOID && !rotation)
+    const bool rot = fn >= PSSO_ROT_ELLIPSOID && fn <= PSSO_ROT_ACKLEY;
+    if (rot && !rotation)
         return bad(PSSO_ERR_ARG, "psso_evaluate: rotated functions need a rotation matrix");
     if ((fn == PSSO_ELLIPSOID || fn == PSSO_ROT_ELLIPSOID) && !weights)
         return bad(PSSO_ERR_ARG, "psso_evaluate: ellipsoid needs weights");
     if (precision != PSSO_PREC_F64 && precision != PSSO_PREC_F32_RECHECK)
         return bad(PSSO_ERR_ARG, "psso_evaluate: unknown precision");
     const bool f32 = precision == PSSO_PREC_F32_RECHECK;
+    if (f32 && fn >= PSSO_SCHWEFEL12)
+        return bad(PSSO_ERR_UNSUPPORTED, "psso_evaluate: this function has FP64 fitness only");
+    std::vector<double> hyper_w;
+    if (fn == PSSO_HYPER_ELLIPSOID) {   // Table 3.2 f2: the ellipsoid with w_j = j + 1
+        hyper_w.resize((size_t)D);
+        for (int64_t j = 0; j < D; ++j) hyper_w[(size_t)j] = (double)(j + 1);
+        weights = hyper_w.data();
+        fn = PSSO_ELLIPSOID;
+    }
     const int nchunks = (int)((D + 3) / 4), Dp = 4 * nchunks;
     int maxc = 1;
     while (maxc < (nchunks + 31) / 32) maxc <<= 1;
@@ -99,7 +109,6 @@ extern "C" psso_status psso_evaluate(psso_fn fn, int64_t N, int64_t D, const dou
         w64[j] = weights ? weights[j] : 0.0;
         w32[j] = (float)w64[j];
     }
-    const bool rot = fn >= PSSO_ROT_ELLIPSOID;
     const size_t nM = rot ? (size_t)D * D : 0;
     std::vector<float> M32(2 * nM);   // float(M), then float(M - float(M))
     for (size_t q = 0; q < nM; ++q) {

@@ -66,12 +66,14 @@ psso_status scratch_on_current_device(NoAllocScratch** out)
     return PSSO_OK;
 }
 
-// Fills the padded shift / weight vectors (zeros beyond D).
-__global__ void fill_scratch(NoAllocScratch* s, const double* shift, const double* weights, int D, int Dp)
+// Fills the padded shift / weight vectors (zeros beyond D); hyper: the
+// weights of the hyper-ellipsoid, w_j = j + 1.
+__global__ void fill_scratch(NoAllocScratch* s, const double* shift, const double* weights, int D, int Dp,
+                             bool hyper)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < Dp; j += gridDim.x * blockDim.x) {
         const double o = (j < D && shift) ? shift[j] : 0.0;
-        const double w = (j < D && weights) ? weights[j] : 0.0;
+        const double w = j >= D ? 0.0 : hyper ? (double)(j + 1) : weights ? weights[j] : 0.0;
         s->o64[j] = o;
         s->o32[j] = (float)o;
         s->w64[j] = w;
@@ -146,7 +148,7 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
                                              int32_t precision, double* f, double* err, void* stream)
 {
     using namespace psso;
-    if (!X || !f || N < 1 || fn < PSSO_SPHERE || fn > PSSO_ROT_ACKLEY) {
+    if (!X || !f || N < 1 || fn < PSSO_SPHERE || fn > PSSO_SCHWEFEL) {
         set_last_error("psso_evaluate_noalloc: need X, f, N >= 1 and a known function");
         return PSSO_ERR_ARG;
     }
@@ -159,10 +161,16 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
         set_last_error("psso_evaluate_noalloc: N above 8 * (2^31 - 1) rows");
         return PSSO_ERR_ARG;
     }
-    if (fn >= PSSO_ROT_ELLIPSOID) {
+    if (fn >= PSSO_ROT_ELLIPSOID && fn <= PSSO_ROT_ACKLEY) {
         set_last_error("psso_evaluate_noalloc: rotated functions are not available through this entry point");
         return PSSO_ERR_UNSUPPORTED;
     }
+    if (precision == PSSO_PREC_F32_RECHECK && fn >= PSSO_SCHWEFEL12) {
+        set_last_error("psso_evaluate_noalloc: this function has FP64 fitness only");
+        return PSSO_ERR_UNSUPPORTED;
+    }
+    const bool hyper = fn == PSSO_HYPER_ELLIPSOID;   // the ellipsoid with w_j = j + 1
+    if (hyper) fn = PSSO_ELLIPSOID;
     if (fn == PSSO_ELLIPSOID && !weights) {
         set_last_error("psso_evaluate_noalloc: the ellipsoid needs weights");
         return PSSO_ERR_ARG;
@@ -187,12 +195,12 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
     in.maxc = maxc;
     in.o64 = s->o64;
     in.o32 = s->o32;
-    in.w64 = weights ? s->w64 : nullptr;
-    in.w32 = weights ? s->w32 : nullptr;
+    in.w64 = (weights || hyper) ? s->w64 : nullptr;
+    in.w32 = (weights || hyper) ? s->w32 : nullptr;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     // clear an earlier, unrelated launch error so that only this call's launches are reported
     (void)cudaGetLastError();
-    fill_scratch<<<(Dp + 255) / 256, 256, 0, cs>>>(s, shift, weights, (int)D, Dp);
+    fill_scratch<<<(Dp + 255) / 256, 256, 0, cs>>>(s, shift, weights, (int)D, Dp, hyper);
     const int wpb = 8;
     const unsigned grid = (unsigned)((N + wpb - 1) / wpb);
     if (precision == PSSO_PREC_F32_RECHECK) eval_noalloc<true><<<grid, 32 * wpb, 0, cs>>>(in, X, N, f, err);

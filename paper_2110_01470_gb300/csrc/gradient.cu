@@ -344,6 +344,11 @@ psso_status fb_check(psso_fn fn, int64_t N, int64_t D, const float* X, const flo
                      const float* weights, const float* rotation)
 {
     using namespace psso;
+    if (fn > PSSO_ROT_ACKLEY && fn <= PSSO_SCHWEFEL) {
+        set_last_error("psso_fitness_forward/backward: no FP32 gradient for this function "
+                       "(the hyper-ellipsoid is ELLIPSOID with weights j + 1)");
+        return PSSO_ERR_UNSUPPORTED;
+    }
     if (!X || !shift || N < 1 || D < 1 || D > 1024 || fn < PSSO_SPHERE || fn > PSSO_ROT_ACKLEY) {
         set_last_error("psso_fitness_forward/backward: need X, shift, N >= 1, 1 <= D <= 1024, a known function");
         return PSSO_ERR_ARG;

@@ -157,8 +157,9 @@ cudaError_t set_smem_of(int v, int mc, size_t smem)
 psso_status check_problem(const psso_problem& pr, int precision, int idx)
 {
     const std::string at = "problem " + std::to_string(idx) + ": ";
-    if (pr.fn < PSSO_SPHERE || pr.fn > PSSO_ROT_ACKLEY) return fail(PSSO_ERR_ARG, at + "unknown function id");
-    if (pr.fn >= PSSO_ROT_ELLIPSOID && !pr.rotation)
+    if (pr.fn < PSSO_SPHERE || pr.fn > PSSO_SCHWEFEL) return fail(PSSO_ERR_ARG, at + "unknown function id");
+    const bool rotated = pr.fn >= PSSO_ROT_ELLIPSOID && pr.fn <= PSSO_ROT_ACKLEY;
+    if (rotated && !pr.rotation)
         return fail(PSSO_ERR_ARG, at + "rotated functions need a rotation matrix");
     if (pr.N < 1 || pr.N > 0x7fffffffLL) return fail(PSSO_ERR_ARG, at + "N must be in [1, 2^31-1]");
     if (pr.D < 1 || pr.D > 32 * MAX_CHUNKS_PER_LANE * 4) return fail(PSSO_ERR_ARG, at + "D must be in [1, 1024]");
@@ -180,10 +181,12 @@ psso_status check_problem(const psso_problem& pr, int precision, int idx)
     if (pr.shift)
         for (int64_t j = 0; j < pr.D; ++j)
             if (!std::isfinite(pr.shift[j])) return fail(PSSO_ERR_ARG, at + "shift must be finite");
-    if (pr.fn >= PSSO_ROT_ELLIPSOID)
+    if (rotated)
         for (int64_t q = 0; q < pr.D * pr.D; ++q)
             if (!std::isfinite(pr.rotation[q])) return fail(PSSO_ERR_ARG, at + "rotation must be finite");
     if (precision == PSSO_PREC_F32_RECHECK) {
+        if (pr.fn >= PSSO_SCHWEFEL12)
+            return fail(PSSO_ERR_UNSUPPORTED, at + "Schwefel 1.2, Griewank, Powell and Schwefel run with FP64 fitness only");
         if (pr.lattice != PSSO_LATTICE_F32)
             return fail(PSSO_ERR_ARG, at + "F32_RECHECK precision needs the F32 lattice");
         if (pr.shift)
@@ -795,9 +798,15 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
         I.o.assign((size_t)I.pr.D, 0.0);
         if (I.pr.shift) std::copy(I.pr.shift, I.pr.shift + I.pr.D, I.o.begin());
         if (I.pr.weights) I.w.assign(I.pr.weights, I.pr.weights + I.pr.D);
-        if (I.pr.fn >= PSSO_ROT_ELLIPSOID) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
+        if (I.pr.fn == PSSO_HYPER_ELLIPSOID) {   // Table 3.2 f2: the ellipsoid with w_j = j + 1
+            I.pr.fn = PSSO_ELLIPSOID;
+            I.w.resize((size_t)I.pr.D);
+            for (int64_t j = 0; j < I.pr.D; ++j) I.w[(size_t)j] = (double)(j + 1);
+        }
+        const bool rot = I.pr.fn >= PSSO_ROT_ELLIPSOID && I.pr.fn <= PSSO_ROT_ACKLEY;
+        if (rot) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
-        I.tc = h->precision == PSSO_PREC_F32_RECHECK && I.pr.fn >= PSSO_ROT_ELLIPSOID &&
+        I.tc = h->precision == PSSO_PREC_F32_RECHECK && rot &&
                (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32));
     }
     {

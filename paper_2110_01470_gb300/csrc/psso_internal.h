@@ -15,7 +15,12 @@ enum FnId {
     FN_ACKLEY = 4,
     FN_ROT_ELLIPSOID = 5,
     FN_ROT_RASTRIGIN = 6,
-    FN_ROT_ACKLEY = 7
+    FN_ROT_ACKLEY = 7,
+    FN_HYPER_ELLIPSOID = 8,   // run as FN_ELLIPSOID with w_j = j + 1
+    FN_SCHWEFEL12 = 9,        // the FP64-only functions: 9 .. 12
+    FN_GRIEWANK = 10,
+    FN_POWELL = 11,
+    FN_SCHWEFEL = 12
 };
 
 constexpr uint32_t TAG_INIT = 1, TAG_RHO = 2, TAG_FRESH = 3;

@@ -359,12 +359,14 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         }
         __syncthreads();
         const size_t o = (size_t)(2 * e + row) * d.Dp;
+        const bool tight = entry_tighten(r.list1[e]);
         for (int t = 0; t < 32; ++t) {
             const int j = jb * 128 + warp * 32 + t;
             if (j >= D) {
                 if (j < d.Dp && lane == 0) {
                     r.z32[o + j] = 0.f;
                     r.ez32[o + j] = 0.f;
+                    if (tight) r.zbuf[o + j] = 0.0;
                 }
                 continue;
             }
@@ -397,7 +399,14 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
             if (lane == 0) {
                 const float z = __fadd_rn(p, sc);
                 r.z32[o + j] = z;
-                r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
+                if (tight) {
+                    // p + sc kept unrounded in FP64 (exact unless their exponents are over 29
+                    // apart: then within 2^-53 |z|): only the Dot2 sum's own error remains
+                    r.zbuf[o + j] = (double)p + (double)sc;
+                    r.ez32[o + j] = __fmaf_ru(cS, S, 0x1p-50f * fabsf(z));
+                } else {
+                    r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
+                }
             }
         }
     }
@@ -430,35 +439,36 @@ __device__ Fit32 fit_refined(const RotDev& r, const InstDev& d, const float* z, 
 }
 
 // Interval of f(z) for an accepted pBest whose value needs tightening: the
-// fitness evaluated in FP64 on the refined z~ (its rounding is below
+// fitness evaluated in FP64 on the refined z~ (the unrounded Dot2 sum p + s,
+// kept in FP64; the FP64 evaluation's own rounding is below
 // 2^-40 (|f| + sum t) at these sizes), widened by the effect of z's error
 // ez: sum |t'(xi)| ez over the terms (ellipsoid w (2|z~| + ez) ez; Rastrigin
 // (2 xi + 20 pi min(1, 2 pi xi)) ez, xi = |z~| + ez; Ackley through the
 // bounds on S1 = sum z^2 and Q = sum sin^2(pi z) as in rot_final).  With the
-// refinement's ez near u |z| this is a few u relative: far tighter than the
-// FP32 evaluation's own rounding bound.
+// Dot2 error near 2 gamma^2 sum |M||d| this is far below 1e-6 relative.
 template <int MAXC>
-__device__ void tight_interval(const RotDev& r, const InstDev& d, const float* z, const float* ez, int lane,
+__device__ void tight_interval(const RotDev& r, const InstDev& d, const double* z, const float* ez, int lane,
                                float& lo, float& hi)
 {
     const int fn = base_fn(r.fn);
     Hot hz = hot_of(d);
     hz.fn = fn;             // the rows hold z already: the unrotated function with o = 0
     hz.o64 = r.zero64;
-    const double f = fit64_row<float>(hz, z, false);
+    const double f = fit64_row<double>(hz, z, false);
     float e = 0.f, eq = 0.f, s1 = 0.f, at = 0.f;
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
         const int c = lane + 32 * q;
         if (c >= d.nchunks) continue;
-        float zv[4], ev[4];
+        double zv[4];
+        float ev[4];
         ld4(z + 4 * c, zv);
         ld4(ez + 4 * c, ev);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = 4 * c + m;
             if (j >= d.D) break;
-            const float az = fabsf(zv[m]), ezj = ev[m], xi = az + ezj;
+            const float az = __double2float_ru(fabs(zv[m])), ezj = ev[m], xi = __fadd_ru(az, ezj);
             if (fn == FN_ELLIPSOID) {
                 const float w = __ldg(r.inst_w32 + j);
                 e = __fadd_ru(e, 1.01f * w * (2.f * az + ezj) * ezj);
@@ -469,7 +479,7 @@ __device__ void tight_interval(const RotDev& r, const InstDev& d, const float* z
             } else {   // Ackley
                 e = __fadd_ru(e, 1.01f * (2.f * az + ezj) * ezj);
                 eq = __fadd_ru(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ezj);
-                s1 = __fadd_rn(s1, __fmul_rn(zv[m], zv[m]));
+                s1 = __fadd_rn(s1, __fmul_rn((float)zv[m], (float)zv[m]));
             }
         }
     }
@@ -504,7 +514,7 @@ __device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int la
     float plo = d.plo[i], phi = d.phi[i];
     if (entry_tighten(raw)) {   // accepted already: intersect the two bounds of f(P) = f(X)
         float tlo, thi;
-        tight_interval<MAXC>(r, d, r.z32 + ox, r.ez32 + ox, lane, tlo, thi);
+        tight_interval<MAXC>(r, d, r.zbuf + ox, r.ez32 + ox, lane, tlo, thi);
         plo = fmaxf(plo, tlo);
         phi = fminf(phi, thi);
         if (lane == 0) {

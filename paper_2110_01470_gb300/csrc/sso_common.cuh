@@ -174,7 +174,9 @@ __device__ __forceinline__ void fresh_chunk(double (&v)[4], uint32_t mask, uint3
 // chunks lane_g + 32 q).  Order: per-lane partials in ascending variable index
 // from +0.0, then an xor butterfly -- bit-identical to the oracle's 32-lane
 // order, since lanes beyond the group hold no variables (their partial is +0.0).
-__device__ __forceinline__ bool is_rotated(int fn) { return fn >= FN_ROT_ELLIPSOID; }
+__device__ __forceinline__ bool is_rotated(int fn) { return fn >= FN_ROT_ELLIPSOID && fn <= FN_ROT_ACKLEY; }
+// Table 3.2's f3, f7, f8, f9: FP64 fitness only.
+__device__ __forceinline__ bool is_fp64_only(int fn) { return fn >= FN_SCHWEFEL12; }
 // Function whose terms a rotated function applies to z = M (x - o).
 __device__ __forceinline__ int base_fn(int fn)
 {
@@ -329,6 +331,87 @@ __device__ __forceinline__ double fit64_impl(const Hot& in, const Pos (&x)[MAXC]
     return -__dadd_rn(__dmul_rn(20.0, B), __dmul_rn(0x1.5bf0a8b145769p+1, C));  // e
 }
 
+// FP64 fitness of Table 3.2's f3 (Schwefel's problem 1.2), f7 (Griewank), f8
+// (Powell) and f9 (Schwefel) on the same lane layout and in the oracle's
+// orders:
+//   f3  prefix sums c_j of z in the blocked order (4-variable block totals,
+//       an inclusive Kogge-Stone scan of the block totals over the lanes of a
+//       128-variable slice, a carry across slices, then a running sum inside
+//       the block), terms c_j^2 summed like every other function's terms;
+//   f7  sum z^2 (lane partials by fma, butterfly) / 4000 and the product of
+//       cos(z_j / sqrt(j + 1)) (lane partials in ascending j, butterfly of
+//       products), f = (1 - P) + S / 4000;
+//   f8  one term per 4-variable block (z = 0 beyond D), lane partials, butterfly;
+//   f9  sum z sin(sqrt|z|) by fma, f = 418.9829 D - S.
+template <class Pos, int MAXC>
+__device__ __noinline__ double fit64_extra(const Hot& in, const RowBuf<Pos, MAXC>& xb, int lane_g,
+                                           unsigned gmask, int G)
+{
+    const auto& x = xb.v;
+    const int D = in.D, nch = in.nchunks, fn = in.fn;
+    double acc = 0.0, prod = 1.0, carry = 0.0;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane_g + 32 * q;
+        double dv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * c + m;
+            dv[m] = (c < nch && j < D) ? __dsub_rn((double)x[q][m], __ldg(in.o64 + j)) : 0.0;
+        }
+        if (fn == FN_SCHWEFEL12) {
+            if (32 * q >= nch) break;            // uniform over the group
+            double v = __dadd_rn(__dadd_rn(__dadd_rn(dv[0], dv[1]), dv[2]), dv[3]);
+            for (int off = 1; off < G; off <<= 1) {
+                const double o = __shfl_up_sync(gmask, v, off, G);
+                if (lane_g >= off) v = __dadd_rn(o, v);
+            }
+            double e = __shfl_up_sync(gmask, v, 1, G);
+            if (lane_g == 0) e = 0.0;
+            const double tot = __shfl_sync(gmask, v, G - 1, G);
+            double run = __dadd_rn(carry, e);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int j = 4 * c + m;
+                if (c < nch && j < D) {
+                    run = __dadd_rn(run, dv[m]);
+                    acc = __fma_rn(run, run, acc);
+                }
+            }
+            carry = __dadd_rn(carry, tot);
+        } else if (c < nch) {
+            if (fn == FN_POWELL) {
+                const double a = __fma_rn(10.0, dv[1], dv[0]), b = __dsub_rn(dv[2], dv[3]);
+                const double cc = __fma_rn(-2.0, dv[2], dv[1]), dd = __dsub_rn(dv[0], dv[3]);
+                const double c2 = __dmul_rn(cc, cc), d2 = __dmul_rn(dd, dd);
+                const double t = __fma_rn(a, a, __fma_rn(__dmul_rn(5.0, b), b,
+                                                         __fma_rn(c2, c2, __dmul_rn(10.0, __dmul_rn(d2, d2)))));
+                acc = __dadd_rn(acc, t);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int j = 4 * c + m;
+                    if (j >= D) break;
+                    const double z = dv[m];
+                    if (fn == FN_GRIEWANK) {
+                        acc = __fma_rn(z, z, acc);
+                        prod = __dmul_rn(prod, cos_rad_f64(__ddiv_rn(z, __dsqrt_rn((double)(j + 1)))));
+                    } else {   // FN_SCHWEFEL
+                        acc = __fma_rn(z, sin_rad_f64(__dsqrt_rn(fabs(z))), acc);
+                    }
+                }
+            }
+        }
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(gmask, acc, off, G));
+    if (fn == FN_GRIEWANK) {
+        for (int off = G >> 1; off > 0; off >>= 1) prod = __dmul_rn(prod, __shfl_xor_sync(gmask, prod, off, G));
+        return __dadd_rn(__dsub_rn(1.0, prod), __ddiv_rn(acc, 4000.0));
+    }
+    if (fn == FN_SCHWEFEL) return __dsub_rn(__dmul_rn(418.9829, (double)D), acc);
+    return acc;
+}
+
 template <class Pos, int MAXC>
 __device__ __noinline__ double fit64_rotated(const Hot& in, const RowBuf<Pos, MAXC>& xb, int lane_g,
                                              unsigned gmask, int G)
@@ -340,12 +423,13 @@ template <class Pos, int MAXC>
 __device__ __forceinline__ double fit64(const Hot& in, const Pos (&x)[MAXC][4], int lane_g, unsigned gmask,
                                         int G)
 {
-    if (is_rotated(in.fn)) {
+    if (is_rotated(in.fn) || is_fp64_only(in.fn)) {
         RowBuf<Pos, MAXC> xb;
 #pragma unroll
         for (int q = 0; q < MAXC; ++q)
 #pragma unroll
             for (int m = 0; m < 4; ++m) xb.v[q][m] = x[q][m];
+        if (is_fp64_only(in.fn)) return fit64_extra<Pos, MAXC>(in, xb, lane_g, gmask, G);
         return fit64_rotated<Pos, MAXC>(in, xb, lane_g, gmask, G);
     }
     return fit64_impl<Pos, MAXC, false>(in, x, lane_g, gmask, G);

@@ -12,7 +12,8 @@ import workload
 pytestmark = pytest.mark.gpu
 
 FNS = ["sphere", "ellipsoid", "rastrigin", "rosenbrock", "ackley", "rot_ellipsoid",
-       "rot_rastrigin", "rot_ackley"]
+       "rot_rastrigin", "rot_ackley", "hyper_ellipsoid", "schwefel12", "griewank", "powell",
+       "schwefel"]
 
 
 def _gpu(lib, p, t, chunks=None, **cfg):

@@ -45,6 +45,13 @@ BOUNDS = {
     "rot_ellipsoid": (-100.0, 100.0),
     "rot_rastrigin": (-5.12, 5.12),
     "rot_ackley": (-32.768, 32.768),
+    "hyper_ellipsoid": (-5.12, 5.12),
+    "schwefel12": (-65.536, 65.536),
+    "griewank": (-600.0, 600.0),
+    "powell": (-4.0, 5.0),
+    # Table 3.2 prints [-5.12, 5.12]; the function's minimum (z_j = 420.9687)
+    # lies in the usual [-500, 500]
+    "schwefel": (-500.0, 500.0),
 }
 
 
