@@ -365,6 +365,26 @@ psso_status psso_fitness_backward(psso_fn fn, int64_t N, int64_t D, const float*
                                   const float* weights, const float* rotation, const float* grad_f,
                                   float* grad_X, void* stream);
 
+/* The same two calls with the rotated functions' products on the tensor
+ * cores: z = M (x - o) for all N rows as one split-BF16 tcgen05 GEMM
+ * (Z = (X - O) M^T), the function and its z-gradient per row from Z, and
+ * the backward product M^T df/dz as a second GEMM (grad_X = G M, G the rows
+ * grad_f[i] df/dz).  Each GEMM output carries a relative error of about
+ * 2^-22 of sum |A_ik| |B_jk|.  `workspace` is caller-owned DEVICE memory,
+ * 256-byte aligned, of at least psso_fitness_workspace_size bytes; the calls
+ * allocate nothing, enqueue on `stream` and return without waiting.  Unrotated
+ * functions (and D < 16) need no workspace and run psso_fitness_forward /
+ * _backward.  Should a tensor-core wait run out (it does not in normal
+ * operation), the outputs are left NaN.  Calls sharing one workspace must be
+ * ordered on one stream. */
+psso_status psso_fitness_workspace_size(psso_fn fn, int64_t N, int64_t D, size_t* bytes);
+psso_status psso_fitness_forward_ws(psso_fn fn, int64_t N, int64_t D, const float* X, const float* shift,
+                                    const float* weights, const float* rotation, float* f, void* workspace,
+                                    size_t ws_bytes, void* stream);
+psso_status psso_fitness_backward_ws(psso_fn fn, int64_t N, int64_t D, const float* X, const float* shift,
+                                     const float* weights, const float* rotation, const float* grad_f,
+                                     float* grad_X, void* workspace, size_t ws_bytes, void* stream);
+
 /* gBest polish (an optional local search; the paper has no counterpart and
  * psso_run never calls it): from instance k's gBest row, `steps` FP32 steps
  * x <- clamp(x - lr df/dx, [lb, ub]) with the gradient of

@@ -150,6 +150,16 @@ def load(path: str = LIB_PATH):
         "psso_fitness_backward": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
+        "psso_fitness_workspace_size": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_size_t)], st),
+        "psso_fitness_forward_ws": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p], st),
+        "psso_fitness_backward_ws": ([ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_size_t, ctypes.c_void_p], st),
         "psso_rotate": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], st),
         "psso_time_kernels": ([H, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32], st),
@@ -389,6 +399,36 @@ def psso_fitness_backward(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr,
         fn = FN[fn]
     _check(load().psso_fitness_backward(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
                                         rotation_ptr, grad_f_ptr, grad_X_ptr, stream))
+
+
+def psso_fitness_workspace_size(fn, N, D):
+    """Device bytes the tensor-core fitness calls need (0: none)."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    n = ctypes.c_size_t(0)
+    _check(load().psso_fitness_workspace_size(int(fn), int(N), int(D), ctypes.byref(n)))
+    return int(n.value)
+
+
+def psso_fitness_forward_ws(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr, f_ptr,
+                            ws_ptr, ws_bytes, stream=None):
+    """psso_fitness_forward with the rotated product on the tensor cores
+    (caller-owned device workspace).  Does not wait."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    _check(load().psso_fitness_forward_ws(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
+                                          rotation_ptr, f_ptr, ws_ptr, int(ws_bytes), stream))
+
+
+def psso_fitness_backward_ws(fn, N, D, X_ptr, shift_ptr, weights_ptr, rotation_ptr, grad_f_ptr,
+                             grad_X_ptr, ws_ptr, ws_bytes, stream=None):
+    """psso_fitness_backward with both rotated products on the tensor cores
+    (caller-owned device workspace).  Does not wait."""
+    if isinstance(fn, str):
+        fn = FN[fn]
+    _check(load().psso_fitness_backward_ws(int(fn), int(N), int(D), X_ptr, shift_ptr, weights_ptr,
+                                           rotation_ptr, grad_f_ptr, grad_X_ptr, ws_ptr,
+                                           int(ws_bytes), stream))
 
 
 def psso_rotate(N, D, X_ptr, shift_ptr, rotation_ptr, Z_ptr, stream=None):

@@ -171,7 +171,7 @@ extern "C" psso_status psso_evaluate_noalloc(psso_fn fn, int64_t N, int64_t D, c
     }
     const bool hyper = fn == PSSO_HYPER_ELLIPSOID;   // the ellipsoid with w_j = j + 1
     if (hyper) fn = PSSO_ELLIPSOID;
-    if (fn == PSSO_ELLIPSOID && !weights) {
+    if (fn == PSSO_ELLIPSOID && !weights && !hyper) {
         set_last_error("psso_evaluate_noalloc: the ellipsoid needs weights");
         return PSSO_ERR_ARG;
     }

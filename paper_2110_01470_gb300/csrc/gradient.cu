@@ -11,7 +11,9 @@
 //               A = sqrt(sum z^2 / D), C = sum cos(2 pi z) / D = 1 - 2 Q / D
 // and for rotated functions df/dx = M^T df/dz.
 #include "psso.h"
+#include "rot_pipeline.h"
 #include "sso_kernel.cuh"
+#include "tc_gemm.cuh"
 
 namespace psso {
 
@@ -336,6 +338,128 @@ cudaError_t launch_polish(const InstDev* inst, int k, int lattice, int owner_ran
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Rotated functions on the tensor cores (the *_ws entry points):
+//   forward   Z = (X - O) M^T        split-BF16 tcgen05 GEMM (tc_gemm.cuh)
+//             f_i from row Z_i       the unrotated function's FP32 kernel, o = 0
+//   backward  G_i = grad_f_i df/dz   from Z (same kernel, its z-gradient)
+//             grad_X = G M           second GEMM, B operand = the planes of M^T
+// Both GEMMs run the six split products of tc_gemm.cuh with FP32
+// accumulation: each output carries a relative error of about 2^-22 of
+// sum |A_ik| |B_jk|, far inside the gradient's own FP32 rounding.
+namespace gtc {
+
+using tc::BM;
+using tc::BN;
+using tc::BK;
+
+// B planes of M^T: row k of the [Jp][Kp] planes holds column k of M.
+__global__ void split_matrix_t(const float* __restrict__ M, int D, int Jp, int Kp, __nv_bfloat16* B)
+{
+    const int k = blockIdx.x;
+    const size_t plane = (size_t)Jp * Kp;
+    for (int j = threadIdx.x; j < Kp; j += blockDim.x) {
+        const float v = (k < D && j < D) ? M[(size_t)j * D + k] : 0.f;
+        __nv_bfloat16 h, m, l;
+        tc::split3(v, h, m, l);
+        const size_t o = (size_t)k * Kp + j;
+        B[o] = h;
+        B[plane + o] = m;
+        B[2 * plane + o] = l;
+    }
+}
+
+// C tile -> out[i * D + j] (rows < N, columns < D).
+struct StoreEpi {
+    float* out;
+    int N, D;
+    __device__ void operator()(int c, const float (&z)[32]) const
+    {
+        const int i = blockIdx.x * BM + threadIdx.x;
+        const int j0 = blockIdx.y * BN + 32 * c;
+        if (i >= N) return;
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+            if (j0 + t < D) out[(size_t)i * D + j0 + t] = z[t];
+    }
+};
+
+__global__ void __launch_bounds__(128, 1)
+    grad_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, tc::GemmArgs a,
+              StoreEpi epi)
+{
+    tc::gemm_tile(&tmA, &tmB, a, epi);
+}
+
+// A planes of G = grad_f_i df/dz for the rows of Z (warp per row of the padded
+// Np x Kp planes; padding zero): the unrotated function's gradient at z.
+template <int MAXC>
+__global__ void gz_split(const Hot hz, const float* Z, int64_t N, const float* gf, int Np, int Kp,
+                         __nv_bfloat16* A)
+{
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= Np) return;
+    const int lane = threadIdx.x & 31;
+    const int D = hz.D;
+    float z[MAXC][4], g[MAXC][4];
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * (lane + 32 * q) + m;
+            z[q][m] = (i < N && j < D) ? Z[i * D + j] : 0.f;
+        }
+    if (i < N) grad32<MAXC, true>(hz, z, g);
+    const float scale = i < N ? gf[i] : 0.f;
+    const size_t plane = (size_t)Np * Kp;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = 4 * (lane + 32 * q) + m;
+            if (j >= Kp) continue;
+            const float v = (i < N && j < D) ? __fmul_rn(scale, g[q][m]) : 0.f;
+            __nv_bfloat16 h, mm, l;
+            tc::split3(v, h, mm, l);
+            const size_t o = (size_t)i * Kp + j;
+            A[o] = h;
+            A[plane + o] = mm;
+            A[2 * plane + o] = l;
+        }
+    // columns beyond this lane layout's reach (Kp may exceed 4 * 32 * MAXC only
+    // when D does not fill the last 64-wide block): zero them
+    for (int j = 128 * MAXC + lane; j < Kp; j += 32) {
+        const size_t o = (size_t)i * Kp + j;
+        A[o] = A[plane + o] = A[2 * plane + o] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// Workspace layout of the tensor-core path (byte offsets, 256-aligned).
+struct WsLayout {
+    int Np, Jp, Kp;
+    size_t a, b, bt, mn, z, zero, status, total;
+};
+inline size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+inline WsLayout ws_layout(int64_t N, int64_t D)
+{
+    WsLayout w{};
+    w.Np = (int)((N + BM - 1) / BM * BM);
+    w.Jp = (int)((D + BN - 1) / BN * BN);
+    w.Kp = (int)((D + BK - 1) / BK * BK);
+    size_t off = 0;
+    auto take = [&](size_t n) { const size_t at = off; off = al256(off + n); return at; };
+    w.a = take((size_t)3 * w.Np * w.Kp * 2);
+    w.b = take((size_t)3 * w.Jp * w.Kp * 2);
+    w.bt = take((size_t)3 * w.Jp * w.Kp * 2);
+    w.mn = take((size_t)w.Jp * 4);
+    w.z = take((size_t)N * D * 4);
+    w.zero = take((size_t)(D + 4) * 4);
+    w.status = take(4);
+    w.total = off;
+    return w;
+}
+
+}  // namespace gtc
 }  // namespace psso
 
 namespace {
@@ -424,6 +548,152 @@ extern "C" psso_status psso_fitness_backward(psso_fn fn, int64_t N, int64_t D, c
         in, X, N, grad_f, nullptr, grad_X);
     if (cudaGetLastError() != cudaSuccess) {
         set_last_error("psso_fitness_backward: launch failed");
+        return PSSO_ERR_CUDA;
+    }
+    return PSSO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core entry points (rotated functions; the others run the warp kernels
+// above and need no workspace).
+namespace {
+
+bool uses_tc(psso_fn fn, int64_t D) { return fn >= PSSO_ROT_ELLIPSOID && fn <= PSSO_ROT_ACKLEY && D >= 16; }
+
+psso::Hot base_hot(psso_fn fn, int64_t D, const float* zero, const float* weights)
+{
+    psso::Hot h = fb_hot(fn, D, zero, weights, nullptr);
+    h.fn = fn == PSSO_ROT_ELLIPSOID ? PSSO_ELLIPSOID : fn == PSSO_ROT_RASTRIGIN ? PSSO_RASTRIGIN : PSSO_ACKLEY;
+    return h;
+}
+
+// Operand planes of M (and of M^T for the backward pass), d = x - o, and Z.
+psso_status tc_forward_z(int64_t N, int64_t D, const float* X, const float* shift, const float* rotation,
+                         char* ws, const psso::gtc::WsLayout& L, bool transposed, cudaStream_t s,
+                         CUtensorMap* tb_t)
+{
+    using namespace psso;
+    auto* A = reinterpret_cast<__nv_bfloat16*>(ws + L.a);
+    auto* B = reinterpret_cast<__nv_bfloat16*>(ws + L.b);
+    auto* Bt = reinterpret_cast<__nv_bfloat16*>(ws + L.bt);
+    CUtensorMap ta, tb;
+    if (!tc::make_tmap_bf16(&ta, A, L.Kp, 3 * L.Np) || !tc::make_tmap_bf16(&tb, B, L.Kp, 3 * L.Jp) ||
+        (transposed && !tc::make_tmap_bf16(tb_t, Bt, L.Kp, 3 * L.Jp))) {
+        set_last_error("psso_fitness_*_ws: cuTensorMapEncodeTiled failed");
+        return PSSO_ERR_CUDA;
+    }
+    float* Z = reinterpret_cast<float*>(ws + L.z);
+    int* status = reinterpret_cast<int*>(ws + L.status);
+    if (cudaMemsetAsync(ws + L.zero, 0, (size_t)(D + 4) * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, 4, s) != cudaSuccess ||
+        // a GEMM whose wait runs out writes nothing: its outputs then read NaN
+        cudaMemsetAsync(Z, 0xff, (size_t)N * D * 4, s) != cudaSuccess ||
+        tc::launch_split_matrix(rotation, (int)D, L.Jp, L.Kp, B, reinterpret_cast<float*>(ws + L.mn), s) !=
+            cudaSuccess ||
+        tc::launch_split_rows(X, shift, (int)N, (int)D, L.Np, L.Kp, A, s) != cudaSuccess) {
+        set_last_error("psso_fitness_*_ws: operand preparation failed");
+        return PSSO_ERR_CUDA;
+    }
+    if (transposed) gtc::split_matrix_t<<<L.Jp, 256, 0, s>>>(rotation, (int)D, L.Jp, L.Kp, Bt);
+    cudaFuncSetAttribute(gtc::grad_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    tc::GemmArgs ga{L.Np, L.Jp, L.Kp, status};
+    gtc::grad_gemm<<<dim3(L.Np / psso::tc::BM, L.Jp / psso::tc::BN), 128, tc::SMEM_BYTES, s>>>(ta, tb, ga,
+                                                                           gtc::StoreEpi{Z, (int)N, (int)D});
+    if (cudaGetLastError() != cudaSuccess) {
+        set_last_error("psso_fitness_*_ws: GEMM launch failed");
+        return PSSO_ERR_CUDA;
+    }
+    return PSSO_OK;
+}
+
+}  // namespace
+
+extern "C" psso_status psso_fitness_workspace_size(psso_fn fn, int64_t N, int64_t D, size_t* bytes)
+{
+    using namespace psso;
+    if (!bytes || N < 1 || D < 1 || D > 1024) {
+        set_last_error("psso_fitness_workspace_size: need bytes, N >= 1, 1 <= D <= 1024");
+        return PSSO_ERR_ARG;
+    }
+    *bytes = uses_tc(fn, D) ? gtc::ws_layout(N, D).total : 0;
+    return PSSO_OK;
+}
+
+extern "C" psso_status psso_fitness_forward_ws(psso_fn fn, int64_t N, int64_t D, const float* X,
+                                               const float* shift, const float* weights, const float* rotation,
+                                               float* f, void* workspace, size_t ws_bytes, void* stream)
+{
+    using namespace psso;
+    if (!uses_tc(fn, D)) return psso_fitness_forward(fn, N, D, X, shift, weights, rotation, f, stream);
+    psso_status st = fb_check(fn, N, D, X, shift, weights, rotation);
+    if (st != PSSO_OK) return st;
+    const gtc::WsLayout L = gtc::ws_layout(N, D);
+    if (!f || !workspace || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_last_error("psso_fitness_forward_ws: need f and a 256-byte aligned workspace of "
+                       "psso_fitness_workspace_size bytes");
+        return PSSO_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    st = tc_forward_z(N, D, X, shift, rotation, ws, L, false, s, nullptr);
+    if (st != PSSO_OK) return st;
+    const Hot hz = base_hot(fn, D, reinterpret_cast<const float*>(ws + L.zero), weights);
+    const int wpb = 8;
+    fitness_fb<false><<<(unsigned)((N + wpb - 1) / wpb), 32 * wpb, 0, s>>>(
+        hz, reinterpret_cast<const float*>(ws + L.z), N, nullptr, f, nullptr);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_last_error("psso_fitness_forward_ws: launch failed");
+        return PSSO_ERR_CUDA;
+    }
+    return PSSO_OK;
+}
+
+extern "C" psso_status psso_fitness_backward_ws(psso_fn fn, int64_t N, int64_t D, const float* X,
+                                                const float* shift, const float* weights,
+                                                const float* rotation, const float* grad_f, float* grad_X,
+                                                void* workspace, size_t ws_bytes, void* stream)
+{
+    using namespace psso;
+    if (!uses_tc(fn, D))
+        return psso_fitness_backward(fn, N, D, X, shift, weights, rotation, grad_f, grad_X, stream);
+    psso_status st = fb_check(fn, N, D, X, shift, weights, rotation);
+    if (st != PSSO_OK) return st;
+    const gtc::WsLayout L = gtc::ws_layout(N, D);
+    if (!grad_f || !grad_X || !workspace || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_last_error("psso_fitness_backward_ws: need grad_f, grad_X and a 256-byte aligned workspace of "
+                       "psso_fitness_workspace_size bytes");
+        return PSSO_ERR_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    CUtensorMap tbt;
+    st = tc_forward_z(N, D, X, shift, rotation, ws, L, true, s, &tbt);
+    if (st != PSSO_OK) return st;
+    const Hot hz = base_hot(fn, D, reinterpret_cast<const float*>(ws + L.zero), weights);
+    auto* A = reinterpret_cast<__nv_bfloat16*>(ws + L.a);   // reused: the planes of G
+    const int wpb = 8;
+    const unsigned grid = (unsigned)((L.Np + wpb - 1) / wpb);
+    const float* Z = reinterpret_cast<const float*>(ws + L.z);
+    switch (hz.maxc) {
+    case 1: gtc::gz_split<1><<<grid, 32 * wpb, 0, s>>>(hz, Z, N, grad_f, L.Np, L.Kp, A); break;
+    case 2: gtc::gz_split<2><<<grid, 32 * wpb, 0, s>>>(hz, Z, N, grad_f, L.Np, L.Kp, A); break;
+    case 4: gtc::gz_split<4><<<grid, 32 * wpb, 0, s>>>(hz, Z, N, grad_f, L.Np, L.Kp, A); break;
+    default: gtc::gz_split<8><<<grid, 32 * wpb, 0, s>>>(hz, Z, N, grad_f, L.Np, L.Kp, A); break;
+    }
+    CUtensorMap ta;
+    if (!tc::make_tmap_bf16(&ta, A, L.Kp, 3 * L.Np)) {
+        set_last_error("psso_fitness_backward_ws: cuTensorMapEncodeTiled failed");
+        return PSSO_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(grad_X, 0xff, (size_t)N * D * 4, s) != cudaSuccess) {
+        set_last_error("psso_fitness_backward_ws: memset failed");
+        return PSSO_ERR_CUDA;
+    }
+    tc::GemmArgs ga{L.Np, L.Jp, L.Kp, reinterpret_cast<int*>(ws + L.status)};
+    gtc::grad_gemm<<<dim3(L.Np / psso::tc::BM, L.Jp / psso::tc::BN), 128, tc::SMEM_BYTES, s>>>(ta, tbt, ga,
+                                                                           gtc::StoreEpi{grad_X, (int)N, (int)D});
+    if (cudaGetLastError() != cudaSuccess) {
+        set_last_error("psso_fitness_backward_ws: launch failed");
         return PSSO_ERR_CUDA;
     }
     return PSSO_OK;

@@ -84,5 +84,8 @@ cudaError_t configure();
 namespace tc {
 cudaError_t launch_split_matrix(const float* M32, int D, int Jp, int Kp, __nv_bfloat16* B, float* mnorm,
                                 cudaStream_t s);
+// A planes of d = x - o for N plain rows of D floats (zero padding to Np x Kp).
+cudaError_t launch_split_rows(const float* X, const float* o, int N, int D, int Np, int Kp, __nv_bfloat16* A,
+                              cudaStream_t s);
 }  // namespace tc
 }  // namespace psso

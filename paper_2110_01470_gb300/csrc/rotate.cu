@@ -92,6 +92,13 @@ cudaError_t launch_split_matrix(const float* M32, int D, int Jp, int Kp, __nv_bf
     return cudaGetLastError();
 }
 
+cudaError_t launch_split_rows(const float* X, const float* o, int N, int D, int Np, int Kp, __nv_bfloat16* A,
+                              cudaStream_t s)
+{
+    split_rows<<<(Np + 7) / 8, 256, 0, s>>>(X, o, N, D, Np, Kp, A);
+    return cudaGetLastError();
+}
+
 struct ZEpi {
     float* Z;
     int N, D;

@@ -41,7 +41,9 @@ def _dev(a):
     return None if a is None else torch.tensor(a, dtype=torch.float32, device="cuda")
 
 
-def _forward_backward(lib, fn, X, o, w, M, grad_f=None):
+def _forward_backward(lib, fn, X, o, w, M, grad_f=None, impl="warp"):
+    """impl "warp": psso_fitness_forward / _backward (CUDA cores); "tc": the
+    *_ws calls (rotated products on the tensor cores, device workspace)."""
     N, D = X.shape
     Xd, od, wd, Md = _dev(X), _dev(o), _dev(w), _dev(M)
     f = torch.empty(N, dtype=torch.float32, device="cuda")
@@ -49,12 +51,23 @@ def _forward_backward(lib, fn, X, o, w, M, grad_f=None):
     gf = torch.ones(N, dtype=torch.float32, device="cuda") if grad_f is None else _dev(grad_f)
     ptr = lambda t: None if t is None else t.data_ptr()
     s = torch.cuda.current_stream().cuda_stream
-    lib.psso_fitness_forward(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
-                             f.data_ptr(), s)
-    lib.psso_fitness_backward(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
-                              gf.data_ptr(), gX.data_ptr(), s)
+    if impl == "warp":
+        lib.psso_fitness_forward(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
+                                 f.data_ptr(), s)
+        lib.psso_fitness_backward(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
+                                  gf.data_ptr(), gX.data_ptr(), s)
+    else:
+        nws = lib.psso_fitness_workspace_size(fn, N, D)
+        ws = torch.empty(max(nws, 1), dtype=torch.uint8, device="cuda")
+        lib.psso_fitness_forward_ws(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
+                                    f.data_ptr(), ws.data_ptr(), nws, s)
+        lib.psso_fitness_backward_ws(fn, N, D, Xd.data_ptr(), od.data_ptr(), ptr(wd), ptr(Md),
+                                     gf.data_ptr(), gX.data_ptr(), ws.data_ptr(), nws, s)
     torch.cuda.synchronize()
     return f.cpu().numpy().astype(np.float64), gX.cpu().numpy().astype(np.float64)
+
+
+IMPLS = ["warp", "tc"]
 
 
 def _plain_torch(fn, X, o, w, M):
@@ -81,26 +94,30 @@ def _rot_tol(fn, rot_tol, tol):
     return rot_tol if fn.startswith("rot_") else tol
 
 
+@pytest.mark.parametrize("impl", IMPLS)
 @pytest.mark.parametrize("fn", ALL_FNS)
 @pytest.mark.parametrize("D", [1, 37, 256, 1024])
-def test_forward_matches_oracle(lib, fn, D):
+def test_forward_matches_oracle(lib, fn, D, impl):
     p, o, w, M = _f32_problem(fn, D, 5 + D)
     X = _points(fn, 70, D, 100 + D)
-    f, _ = _forward_backward(lib, fn, X, o, w, M)
+    f, _ = _forward_backward(lib, fn, X, o, w, M, impl=impl)
     ref = np.array([oracle.fitness(fn, x, o, w, M) for x in X])
     rel = np.abs(f - ref) / np.maximum(np.abs(ref), 1e-30)
     assert np.all(np.isfinite(f))
     assert rel.max() <= _rot_tol(fn, 1e-3, 2e-5), rel.max()
 
 
+@pytest.mark.parametrize("impl", IMPLS)
 @pytest.mark.parametrize("fn", ALL_FNS)
-def test_gradient_central_differences(lib, fn):
+def test_gradient_central_differences(lib, fn, impl):
     """df/dx against FP64 central differences (h = 1e-6) of the oracle's
     fitness, 64 random particles, D = 256."""
+    if impl == "tc" and not fn.startswith("rot_"):
+        pytest.skip("the *_ws calls run the warp kernels for unrotated functions")
     D, N, h = 256, 64, 1e-6
     p, o, w, M = _f32_problem(fn, D, 77)
     X = _points(fn, N, D, 78)
-    _, g = _forward_backward(lib, fn, X, o, w, M)
+    _, g = _forward_backward(lib, fn, X, o, w, M, impl=impl)
     worst = 0.0
     for i in range(N):
         fd = np.empty(D)
@@ -115,14 +132,15 @@ def test_gradient_central_differences(lib, fn):
     assert worst <= _rot_tol(fn, 2e-3, 1e-4), worst
 
 
+@pytest.mark.parametrize("impl", IMPLS)
 @pytest.mark.parametrize("fn", ALL_FNS)
 @pytest.mark.parametrize("D", [1, 5, 131, 1024])
-def test_gradient_torch_autograd(lib, fn, D):
+def test_gradient_torch_autograd(lib, fn, D, impl):
     """df/dx against torch's FP64 autograd of the textbook definition."""
     p, o, w, M = _f32_problem(fn, D, 9 + D)
     X = _points(fn, 33, D, 10 + D)
     gf = np.random.default_rng(D).uniform(-2, 2, size=33).astype(np.float32).astype(np.float64)
-    _, g = _forward_backward(lib, fn, X, o, w, M, grad_f=gf)
+    _, g = _forward_backward(lib, fn, X, o, w, M, grad_f=gf, impl=impl)
     Xt = torch.tensor(X, dtype=torch.float64, requires_grad=True)
     tw = None if w is None else torch.tensor(w)
     tM = None if M is None else torch.tensor(M)
@@ -134,10 +152,11 @@ def test_gradient_torch_autograd(lib, fn, D):
     assert err <= _rot_tol(fn, 2e-3, 1e-4), err
 
 
-def test_gradient_at_optimum_is_zero(lib):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_gradient_at_optimum_is_zero(lib, impl):
     for fn in ALL_FNS:
         p, o, w, M = _f32_problem(fn, 64, 12)
-        f, g = _forward_backward(lib, fn, o[None, :].copy(), o, w, M)
+        f, g = _forward_backward(lib, fn, o[None, :].copy(), o, w, M, impl=impl)
         assert f[0] == 0.0, fn
         assert np.all(g == 0.0), fn
 
@@ -151,7 +170,7 @@ def test_autograd_function(lib):
     f = fitness(X, "rot_rastrigin", _dev(o), rotation=_dev(M))
     (f * c).sum().backward()
     f2, g = _forward_backward(lib, "rot_rastrigin", X.detach().cpu().numpy().astype(np.float64),
-                              o, None, M, grad_f=c.cpu().numpy().astype(np.float64))
+                              o, None, M, grad_f=c.cpu().numpy().astype(np.float64), impl="tc")
     assert np.array_equal(f.detach().cpu().numpy(), f2.astype(np.float32))
     assert np.array_equal(X.grad.cpu().numpy(), g.astype(np.float32))
 
@@ -297,3 +316,33 @@ def test_polish_arguments_rejected(lib):
                 lib.psso_polish(h, *args)
     finally:
         lib.psso_destroy(h)
+
+
+@pytest.mark.parametrize("fn", ["rot_ellipsoid", "rot_rastrigin", "rot_ackley"])
+@pytest.mark.parametrize("N,D", [(1, 16), (129, 100), (300, 257), (4096, 256)])
+def test_tensor_core_gradient_matches_warp_kernels(lib, fn, N, D):
+    """The tensor-core forward / backward against the CUDA-core kernels on the
+    same rows: both FP32, so they agree to the GEMM's split-BF16 accuracy."""
+    p, o, w, M = _f32_problem(fn, D, 40 + D)
+    X = _points(fn, N, D, 41 + D)
+    gf = np.random.default_rng(N).uniform(-2, 2, size=N).astype(np.float32).astype(np.float64)
+    fw, gw = _forward_backward(lib, fn, X, o, w, M, grad_f=gf, impl="warp")
+    ft, gt = _forward_backward(lib, fn, X, o, w, M, grad_f=gf, impl="tc")
+    assert np.all(np.isfinite(ft)) and np.all(np.isfinite(gt))
+    assert np.max(np.abs(ft - fw) / np.maximum(np.abs(fw), 1e-30)) <= 2e-4
+    scale = np.maximum(np.abs(gw).max(1, keepdims=True), 1e-30)
+    assert (np.abs(gt - gw) / scale).max() <= 2e-4
+
+
+def test_tensor_core_workspace_checked(lib):
+    X = torch.zeros((4, 64), device="cuda")
+    o = torch.zeros(64, device="cuda")
+    M = torch.eye(64, device="cuda")
+    f = torch.empty(4, device="cuda")
+    n = lib.psso_fitness_workspace_size("rot_rastrigin", 4, 64)
+    assert n > 0 and lib.psso_fitness_workspace_size("rastrigin", 4, 64) == 0
+    ws = torch.empty(n, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.PssoError) as e:
+        lib.psso_fitness_forward_ws("rot_rastrigin", 4, 64, X.data_ptr(), o.data_ptr(), None,
+                                    M.data_ptr(), f.data_ptr(), ws.data_ptr(), n - 1)
+    assert e.value.status == lib.PSSO_ERR_ARG
