@@ -595,7 +595,13 @@ psso_status tc_forward_z(int64_t N, int64_t D, const float* X, const float* shif
         return PSSO_ERR_CUDA;
     }
     if (transposed) gtc::split_matrix_t<<<L.Jp, 256, 0, s>>>(rotation, (int)D, L.Jp, L.Kp, Bt);
-    cudaFuncSetAttribute(gtc::grad_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    static thread_local int smem_set_for = -1;   // the attribute is per device
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (smem_set_for != dev) {
+        cudaFuncSetAttribute(gtc::grad_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+        smem_set_for = dev;
+    }
     tc::GemmArgs ga{L.Np, L.Jp, L.Kp, status};
     gtc::grad_gemm<<<dim3(L.Np / psso::tc::BM, L.Jp / psso::tc::BN), 128, tc::SMEM_BYTES, s>>>(ta, tb, ga,
                                                                            gtc::StoreEpi{Z, (int)N, (int)D});

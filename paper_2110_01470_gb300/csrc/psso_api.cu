@@ -1070,6 +1070,12 @@ psso_status psso_get_state(psso_handle h, int32_t instance, double* X, double* P
     const HostInst& I = h->inst[instance];
     if (X && (st = copy_row(h, I, I.off_X, I.pr.N, X)) != PSSO_OK) return st;
     if (P && (st = copy_row(h, I, I.off_P, I.pr.N, P)) != PSSO_OK) return st;
+    if (pF && I.tc) {
+        // the tensor-core pipeline keeps most pBest values as certified intervals;
+        // those too wide for 1e-6 relative get their FP64 value before the read
+        CUDA_TRY(rot::exact_values_for_read(I.rh, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
     if (pF) {
         const size_t N = (size_t)I.pr.N;
         CUDA_TRY(cudaMemcpy(pF, h->arena + I.off_pf64, N * 8, cudaMemcpyDeviceToHost));

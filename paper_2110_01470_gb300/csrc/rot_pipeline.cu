@@ -65,13 +65,6 @@ __global__ void set_gen(RotCtl* ctl, long long g)
     ctl->rck = 0;
 }
 
-// List entries with this bit set are accepted pBests (P = X) whose value
-// only needs a tighter interval: no decision is left, only the X row is
-// re-evaluated (N < 2^31, so the index fits the other 31 bits).
-constexpr int32_t TIGHTEN = (int32_t)0x80000000u;
-__device__ __forceinline__ int32_t entry_index(int32_t v) { return v & 0x7fffffff; }
-__device__ __forceinline__ bool entry_tighten(int32_t v) { return v < 0; }
-
 // ---- 1. update --------------------------------------------------------------
 template <int MAXC>
 __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
@@ -309,9 +302,6 @@ __global__ void rot_decide(const RotDev r)
         }
         if (lane == 0) {
             if (undecided) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i;
-            // an accepted value whose GEMM bounds are too wide for 1e-6 relative
-            // goes to the refinement too, marked: only its X row is refined
-            if (write && too_wide(r.fn, lo, hi)) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i | TIGHTEN;
             if (accept) atomicAdd(&blk_acc, 1ull);
         }
     }
@@ -346,8 +336,8 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         const int jb = (int)(it % nJb);
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
-        const int32_t i = entry_index(r.list1[e]);
-        if (row == 1 && (entry_tighten(r.list1[e]) || (d.pflag[i] & 1u))) continue;   // uniform over the block
+        const int32_t i = r.list1[e];
+        if (row == 1 && (d.pflag[i] & 1u)) continue;     // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
         __syncthreads();
         for (int k = threadIdx.x; k < D; k += blockDim.x) {
@@ -359,14 +349,12 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         }
         __syncthreads();
         const size_t o = (size_t)(2 * e + row) * d.Dp;
-        const bool tight = entry_tighten(r.list1[e]);
         for (int t = 0; t < 32; ++t) {
             const int j = jb * 128 + warp * 32 + t;
             if (j >= D) {
                 if (j < d.Dp && lane == 0) {
                     r.z32[o + j] = 0.f;
                     r.ez32[o + j] = 0.f;
-                    if (tight) r.zbuf[o + j] = 0.0;
                 }
                 continue;
             }
@@ -399,14 +387,7 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
             if (lane == 0) {
                 const float z = __fadd_rn(p, sc);
                 r.z32[o + j] = z;
-                if (tight) {
-                    // p + sc kept unrounded in FP64 (exact unless their exponents are over 29
-                    // apart: then within 2^-53 |z|): only the Dot2 sum's own error remains
-                    r.zbuf[o + j] = (double)p + (double)sc;
-                    r.ez32[o + j] = __fmaf_ru(cS, S, 0x1p-50f * fabsf(z));
-                } else {
-                    r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
-                }
+                r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
             }
         }
     }
@@ -438,93 +419,13 @@ __device__ Fit32 fit_refined(const RotDev& r, const InstDev& d, const float* z, 
     return rot_final(fn, d.D, s, s2, e, eq, (float)(4 * MAXC + 5 + 2));
 }
 
-// Interval of f(z) for an accepted pBest whose value needs tightening: the
-// fitness evaluated in FP64 on the refined z~ (the unrounded Dot2 sum p + s,
-// kept in FP64; the FP64 evaluation's own rounding is below
-// 2^-40 (|f| + sum t) at these sizes), widened by the effect of z's error
-// ez: sum |t'(xi)| ez over the terms (ellipsoid w (2|z~| + ez) ez; Rastrigin
-// (2 xi + 20 pi min(1, 2 pi xi)) ez, xi = |z~| + ez; Ackley through the
-// bounds on S1 = sum z^2 and Q = sum sin^2(pi z) as in rot_final).  With the
-// Dot2 error near 2 gamma^2 sum |M||d| this is far below 1e-6 relative.
-template <int MAXC>
-__device__ void tight_interval(const RotDev& r, const InstDev& d, const double* z, const float* ez, int lane,
-                               float& lo, float& hi)
-{
-    const int fn = base_fn(r.fn);
-    Hot hz = hot_of(d);
-    hz.fn = fn;             // the rows hold z already: the unrotated function with o = 0
-    hz.o64 = r.zero64;
-    const double f = fit64_row<double>(hz, z, false);
-    float e = 0.f, eq = 0.f, s1 = 0.f, at = 0.f;
-#pragma unroll
-    for (int q = 0; q < MAXC; ++q) {
-        const int c = lane + 32 * q;
-        if (c >= d.nchunks) continue;
-        double zv[4];
-        float ev[4];
-        ld4(z + 4 * c, zv);
-        ld4(ez + 4 * c, ev);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int j = 4 * c + m;
-            if (j >= d.D) break;
-            const float az = __double2float_ru(fabs(zv[m])), ezj = ev[m], xi = __fadd_ru(az, ezj);
-            if (fn == FN_ELLIPSOID) {
-                const float w = __ldg(r.inst_w32 + j);
-                e = __fadd_ru(e, 1.01f * w * (2.f * az + ezj) * ezj);
-                at = __fadd_ru(at, 1.01f * w * xi * xi);
-            } else if (fn == FN_RASTRIGIN) {
-                e = __fadd_ru(e, 1.01f * (2.f * xi + 62.8318558f * fminf(1.f, 6.28318548f * xi)) * ezj);
-                at = __fadd_ru(at, xi * xi + 20.f);
-            } else {   // Ackley
-                e = __fadd_ru(e, 1.01f * (2.f * az + ezj) * ezj);
-                eq = __fadd_ru(eq, 1.01f * 3.14159275f * fminf(1.f, 6.28318548f * xi) * ezj);
-                s1 = __fadd_rn(s1, __fmul_rn((float)zv[m], (float)zv[m]));
-            }
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        e = __fadd_ru(e, __shfl_xor_sync(0xffffffffu, e, off));
-        eq = __fadd_ru(eq, __shfl_xor_sync(0xffffffffu, eq, off));
-        s1 = __fadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, off));
-        at = __fadd_ru(at, __shfl_xor_sync(0xffffffffu, at, off));
-    }
-    float E;
-    if (fn != FN_ACKLEY) {
-        E = 1.1f * e + 0x1p-40f * (at + (float)fabs(f));
-    } else {
-        // S1 from the float sum: at most (K + L + 2) u relative off, K <= 32, L = 5
-        const float Df = (float)d.D;
-        const float s1lo = s1 * (1.f - 48.f * 0x1p-24f);
-        const float f1 = 1.0001f * -20.f * expm1_f32(-0.2f * __fsqrt_rn(s1 / Df));
-        const float d1 = (e <= 0.5f * s1lo) ? 1.5f * f1 * e / s1lo : 4.f * __fsqrt_ru(e / Df);
-        E = 1.1f * (d1 + (2.f * 2.7182818f / Df) * eq) + 0x1p-40f * ((float)fabs(f) + 25.f);
-    }
-    lo = f64_to_f32_rd(f - (double)E);
-    hi = f64_to_f32_ru(f + (double)E);
-}
-
 template <int MAXC>
 __device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int lane)
 {
-    const int32_t raw = r.list1[e];
-    const int32_t i = entry_index(raw);
+    const int32_t i = r.list1[e];
     const int64_t g = r.ctl->gen;
     const size_t ox = (size_t)(2 * e) * d.Dp, op = ox + d.Dp;
     float plo = d.plo[i], phi = d.phi[i];
-    if (entry_tighten(raw)) {   // accepted already: intersect the two bounds of f(P) = f(X)
-        float tlo, thi;
-        tight_interval<MAXC>(r, d, r.zbuf + ox, r.ez32 + ox, lane, tlo, thi);
-        plo = fmaxf(plo, tlo);
-        phi = fminf(phi, thi);
-        if (lane == 0) {
-            d.plo[i] = plo;
-            d.phi[i] = phi;
-            if (too_wide(r.fn, plo, phi)) r.list3[atomicAdd(&r.ctl->n3, 1u)] = raw;
-            atomicAdd(&r.ctl->refined, 1ull);
-        }
-        return;
-    }
     const Fit32 fx = fit_refined<MAXC>(r, d, r.z32 + ox, r.ez32 + ox, lane);
     const float lox = __fsub_rd(fx.f, fx.E), hix = __fadd_ru(fx.f, fx.E);
     const bool have_p = (d.pflag[i] & 1u) != 0;
@@ -596,7 +497,7 @@ __global__ void rot_z64(const RotDev r, int which)
 {
     __shared__ double dsh[1024];
     const InstDev& d = *r.inst;
-    const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;
+    const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;   // which 2 or 4: list 2
     const int D = r.D;
     const int nJb = (D + 127) / 128;
     const long long items = (long long)n * 2 * nJb;
@@ -604,9 +505,8 @@ __global__ void rot_z64(const RotDev r, int which)
         const int jb = (int)(it % nJb);
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
-        const int32_t raw = which == 1 ? r.list3[e] : r.list2[e];
-        const int32_t i = entry_index(raw);
-        const bool needed = which == 1 ? (row == 0 || (!entry_tighten(raw) && !(d.pflag[i] & 1u))) : row == 1;
+        const int32_t i = which == 1 ? r.list3[e] : r.list2[e];
+        const bool needed = which == 1 ? (row == 0 || !(d.pflag[i] & 1u)) : row == 1;
         if (!needed) continue;          // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
         __syncthreads();
@@ -634,17 +534,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
     const int64_t g = r.ctl->gen;
     const double* zx = r.zbuf + (size_t)(2 * e) * d.Dp;
     const double* zp = zx + d.Dp;
-    if (which == 1 && entry_tighten(r.list3[e])) {   // accepted pBest: its exact value
-        const int32_t i = entry_index(r.list3[e]);
-        const double fx = fit64_row<double>(hz, zx, false);
-        if (lane == 0) {
-            d.pf64[i] = fx;
-            d.pflag[i] = 1u;
-            d.plo[i] = f64_to_f32_rd(fx);
-            d.phi[i] = f64_to_f32_ru(fx);
-            atomicAdd(&r.ctl->rck, 1ull);
-        }
-    } else if (which == 1) {
+    if (which == 1) {
         const int32_t i = r.list3[e];
         const bool have_p = (d.pflag[i] & 1u) != 0;
         const double fx = fit64_row<double>(hz, zx, false);
@@ -669,7 +559,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
             atomicAdd(&r.ctl->rck, have_p ? 1ull : 2ull);
             if (accept) atomicAdd(&r.ctl->acc, 1ull);
         }
-    } else {
+    } else {   // list 2 (which 2: in a generation; 4: on demand, outside the counters)
         const int32_t i = r.list2[e];
         const double fp = fit64_row<double>(hz, zp, false);
         if (lane == 0) {
@@ -677,7 +567,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
             d.pflag[i] = 1u;
             d.plo[i] = f64_to_f32_rd(fp);
             d.phi[i] = f64_to_f32_ru(fp);
-            atomicAdd(&r.ctl->rck, 1ull);
+            if (which == 2) atomicAdd(&r.ctl->rck, 1ull);
         }
     }
 }
@@ -711,7 +601,15 @@ __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
         const Cand b = block_reduce_cand<true>(c, sh);
         if (b.l2 > b.mh) {          // one interval lies below every other: the arg-min
             if (threadIdx.x == 0) {
-                ctl->amb = 0;
+                // the gBest value the generation reports must lie within 1e-6 of
+                // FP64: an interval too wide for that gets the winner's FP64 value
+                // (list 2; the exact pass of phase 1 then keeps the same winner)
+                const bool wide = !b.has1 && too_wide(r.fn, b.l1, b.h1);
+                ctl->amb = wide ? 1 : 0;
+                if (wide) {
+                    r.list2[0] = (int32_t)b.i;
+                    ctl->n2 = 1;
+                }
                 ctl->win_i = b.i;
                 ctl->win_v = b.v;
                 ctl->win_lo = b.l1;
@@ -783,7 +681,33 @@ __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
     }
 }
 
+// ---- values on demand --------------------------------------------------------------------
+// Every pBest whose value is known only by an interval too wide for 1e-6
+// relative goes on list 2; its FP64 value is then computed (rot_z64 and
+// rot_fix with which = 4) -- once, when the state is read.  The trajectory
+// does not change: only the stored intervals become exact.
+__global__ void list_wide(const RotDev r)
+{
+    const InstDev& d = *r.inst;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+        if (!(d.pflag[i] & 1u) && too_wide(r.fn, d.plo[i], d.phi[i]))
+            r.list2[atomicAdd(&r.ctl->n2, 1u)] = (int32_t)i;
+}
+
+__global__ void clear_n2(RotCtl* ctl) { ctl->n2 = 0; }
+
 // ---- host --------------------------------------------------------------------------------
+cudaError_t exact_values_for_read(const RotHost& h, cudaStream_t s)
+{
+    const RotDev& r = h.dev;
+    clear_n2<<<1, 1, 0, s>>>(r.ctl);
+    list_wide<<<(unsigned)std::min<long long>((h.N + 255) / 256, 1024), 256, 0, s>>>(r);
+    rot_z64<<<h.z64_grid, 128, 0, s>>>(r, 4);
+    rot_fix<<<h.fix_grid, 256, 0, s>>>(r, 4);
+    clear_n2<<<1, 1, 0, s>>>(r.ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent_t* ev);
 
 cudaError_t enqueue_generation(const RotHost& h, cudaStream_t s)

@@ -76,6 +76,9 @@ void destroy_graphs(RotHost& h);
 // Enqueues `count` generations (graph replays) on s.
 cudaError_t run_generations(const RotHost& h, long long count, cudaStream_t s);
 cudaError_t build_constants(const RotHost& h, cudaStream_t s);
+// FP64 values of the pBests whose intervals are too wide for 1e-6 relative
+// (before the state is read; enqueued on s after the generations).
+cudaError_t exact_values_for_read(const RotHost& h, cudaStream_t s);
 cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s);
 cudaError_t configure();
 
