@@ -332,13 +332,16 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
     rot = [p for p in problems if p["fn"].startswith("rot_") and p["N"] >= 128 and p["D"] >= 32]
     if prec != "f32" or not rot:
         return None
+    per_instance = []
+    for q in rot:
+        h = psso.psso_create_ex([q], prec, stream=sptr)
+        try:
+            psso.psso_run(h, gens)
+            per_instance.append({"fn": q["fn"], "kernels_ms": psso.psso_time_kernels(h, 0, gens)})
+        finally:
+            psso.psso_destroy(h)
     p = rot[0]
-    h = psso.psso_create_ex([p], prec, stream=sptr)
-    try:
-        psso.psso_run(h, gens)
-        ms = psso.psso_time_kernels(h, 0, gens)
-    finally:
-        psso.psso_destroy(h)
+    ms = per_instance[0]["kernels_ms"]
     N, D = p["N"], p["D"]
     Np, Jp, Kp = -(-N // 128) * 128, -(-D // 128) * 128, -(-D // 64) * 64
     t = ms["gemm_fit"] / 1e3
@@ -354,7 +357,8 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
             "peak_note": f"bf16 sustained {which} (kernel timed inside the generation sequence); "
                          "achieved counts 2 N D^2 algorithmic flops, executed_tflops the six split "
                          "BF16 products over padded extents",
-            "kernels_ms": ms, "instance": {"fn": p["fn"], "N": N, "D": D}}
+            "kernels_ms": ms, "instance": {"fn": p["fn"], "N": N, "D": D},
+            "per_instance": per_instance}
 
 
 def accept_rate(psso, problems, prec, t, sptr, stride=10):

@@ -180,9 +180,7 @@ typedef struct {
                                    persistent kernel)                              */
     int32_t batch_blocks_per_sm;/* batched pipeline: resident blocks per SM of each
                                    step kernel's grid (0 = the occupancy maximum;
-                                   larger values are clamped to it); 1 or 2 also
-                                   selects the streaming kernel's variant with
-                                   registers for 2 blocks per SM                   */
+                                   larger values are clamped to it)                 */
     int32_t flow;               /* psso_flow: 0 = synchronous generations (Alg. 2),
                                    1 = asynchronous generations (Alg. 1)           */
 } psso_config;

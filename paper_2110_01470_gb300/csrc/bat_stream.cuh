@@ -153,12 +153,8 @@ struct StreamAcc<true> {
     }
 };
 
-// MINB: blocks of 256 threads per SM the register allocation is sized for
-// (4: 64 registers, some spilled; 2: 128 registers, no spills, half the warps
-// to hide the row loads).  The autotuner picks between them through
-// psso_config.batch_blocks_per_sm.
-template <class Pos, bool F32R, int MINB>
-__global__ void __launch_bounds__(256, MINB) bat_stream(const BatParams p)
+template <class Pos, bool F32R>
+__global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
 {
     using Val = typename std::conditional<F32R, float, double>::type;
     const int lane = threadIdx.x & 31;
@@ -344,15 +340,11 @@ __global__ void __launch_bounds__(256, MINB) bat_stream(const BatParams p)
     }
 }
 
-// ops 2 / 3: launch / occupancy of the 4-blocks-per-SM variant; 4 / 5: of
-// the 2-blocks-per-SM variant.
 template <class Pos, bool F32R>
 inline cudaError_t bat_stream_entry(int op, const BatParams* p, int grid, int block, cudaStream_t s, int* out)
 {
-    if (op == 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_stream<Pos, F32R, 4>, block, 0);
-    if (op == 5) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_stream<Pos, F32R, 2>, block, 0);
-    if (op == 4) bat_stream<Pos, F32R, 2><<<grid, block, 0, s>>>(*p);
-    else bat_stream<Pos, F32R, 4><<<grid, block, 0, s>>>(*p);
+    if (op == 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_stream<Pos, F32R>, block, 0);
+    bat_stream<Pos, F32R><<<grid, block, 0, s>>>(*p);
     return cudaGetLastError();
 }
 

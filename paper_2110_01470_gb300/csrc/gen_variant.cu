@@ -41,8 +41,7 @@ cudaError_t PSSO_BNAME(PSSO_VARIANT, PSSO_MC)(int op, const BatParams* p, int gr
                                                int* out)
 {
 #if PSSO_MC == 8
-    // ops 2 .. 5: the streaming kernel for wide unrotated rows (launch / occupancy
-    // of its two register budgets)
+    // ops 2 / 3: the streaming kernel for wide unrotated rows (launch / occupancy)
     if (op >= 2) return bat_stream_entry<VPos, kF32R>(op, p, grid, block, s, out);
 #endif
     return bat_entry_mc<VPos, kF32R, PSSO_MC>(op, p, grid, block, s, out);

@@ -85,7 +85,6 @@ struct BatHost {
     struct Class {
         int mc_index = 0, G = 32, grid = 0;
         bool stream = false;       // wide unrotated rows: the streaming kernel
-        bool stream_2pb = false;   // ... in its variant sized for 2 blocks per SM (128 registers)
         int32_t* ids = nullptr;
         int64_t* first = nullptr;
         int32_t n = 0;
@@ -580,7 +579,7 @@ cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s, cudaEvent_t* ev 
     if (ev) cudaEventRecord(ev[q++], s);
     for (const auto& c : h->bat.classes) {
         BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, h->bat.gen, h->bat.cnt};
-        const cudaError_t e = c.stream ? bat_call(h->variant, 3, c.stream_2pb ? 4 : 2, &p, c.grid, 256, s, nullptr)
+        const cudaError_t e = c.stream ? bat_call(h->variant, 3, 2, &p, c.grid, 256, s, nullptr)
                                        : bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
         if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[q++], s);
@@ -652,11 +651,7 @@ psso_status setup_bat(psso_ctx* h)
         cl.ids = reinterpret_cast<int32_t*>(base + oid[c]);
         cl.first = reinterpret_cast<int64_t*>(base + ofirst[c]);
         int bps = 0;
-        // a budget of 1 or 2 blocks per SM selects the streaming kernel's variant with
-        // registers for 2 blocks (no spills); larger budgets the 4-block variant
-        cl.stream_2pb = cl.stream && h->cfg.batch_blocks_per_sm > 0 && h->cfg.batch_blocks_per_sm <= 2;
-        CUDA_TRY(bat_call(h->variant, cl.mc_index, cl.stream ? (cl.stream_2pb ? 5 : 3) : 1, nullptr, 0, 256,
-                          nullptr, &bps));
+        CUDA_TRY(bat_call(h->variant, cl.mc_index, cl.stream ? 3 : 1, nullptr, 0, 256, nullptr, &bps));
         if (h->cfg.batch_blocks_per_sm > 0) bps = std::min(bps, (int)h->cfg.batch_blocks_per_sm);
         const int64_t groups_per_block = cl.stream ? 8 : 256 / cl.G;
         const int64_t need = (cl.total + groups_per_block - 1) / groups_per_block;
