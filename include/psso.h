@@ -268,6 +268,31 @@ psso_status psso_sync(psso_handle h);
 psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* index,
                       double* row);
 
+/* One swarm split over several GPUs: every GPU runs the update, fitness and
+ * pBest step of its own particles, and the gBest is the lowest-index arg-min
+ * over all of them (one exchange per generation).
+ *
+ * psso_create_shard creates a handle for particles first .. first+count-1 of
+ * `problem` (problem->N particles in all): its draws are those of these
+ * particles in the whole swarm, so the union of the shards' runs is the run of
+ * the whole swarm, provided that before every generation each shard is given
+ * the swarm's gBest of the previous generation with psso_set_gbest (value,
+ * global index, row: the minimum over the shards' psso_best by (value, index)).
+ * The shard runs in one block (its gBest row is restored from the handle's
+ * gBest state at every psso_run).  The asynchronous flow cannot be split
+ * (PSSO_ERR_UNSUPPORTED).  Indices the shard reports (psso_best, the log)
+ * are local: add `first`.
+ *
+ * psso_set_gbest replaces the gBest the next generation searches with: FP64
+ * value, an index (stored as given; any label), and the row (host, D values
+ * inside [lb, ub]; floats for the F32 lattice).  Synchronises.  Valid for
+ * shard handles and single-block, tensor-pipeline or batched-pipeline
+ * instances; PSSO_ERR_UNSUPPORTED for an instance spread over several blocks
+ * or the asynchronous flow. */
+psso_status psso_create_shard(const psso_problem* problem, int64_t first, int64_t count,
+                              const psso_config* cfg, psso_handle* out);
+psso_status psso_set_gbest(psso_handle h, int32_t instance, double value, int64_t index, const double* row);
+
 /* Copies positions X (N*D), pBests P (N*D) and pBest fitness pF (N) of one
  * instance to the host (FP64 values; any pointer may be NULL).  In
  * F32_RECHECK mode pF holds the FP64 value where known, else the midpoint of

@@ -169,6 +169,9 @@ def load(path: str = LIB_PATH):
                            ctypes.POINTER(psso_config), ctypes.c_int32,
                            ctypes.POINTER(psso_config), ctypes.POINTER(psso_tune_report)], st),
         "psso_microbench": ([ctypes.POINTER(psso_peaks), ctypes.c_void_p], st),
+        "psso_create_shard": ([ctypes.POINTER(psso_problem), ctypes.c_int64, ctypes.c_int64,
+                               ctypes.POINTER(psso_config), ctypes.POINTER(H)], st),
+        "psso_set_gbest": ([H, ctypes.c_int32, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -259,6 +262,22 @@ def psso_create_ex(problems, precision=PSSO_PREC_F64, **config):
     h = ctypes.c_void_p()
     _check(load().psso_create_ex(arr, len(problems), ctypes.byref(cfg), ctypes.byref(h)))
     return h
+
+
+def psso_create_shard(problem, first, count, precision=PSSO_PREC_F64, **config):
+    """Handle for particles first .. first+count-1 of one swarm (see psso.h)."""
+    arr, keep = _problems([problem])
+    cfg = _config(precision, config)
+    h = ctypes.c_void_p()
+    _check(load().psso_create_shard(arr, int(first), int(count), ctypes.byref(cfg),
+                                    ctypes.byref(h)))
+    return h
+
+
+def psso_set_gbest(h, instance, value, index, row):
+    """Replace the gBest the next generation searches with (value, index, row)."""
+    row = np.ascontiguousarray(row, dtype=np.float64)
+    _check(load().psso_set_gbest(h, int(instance), float(value), int(index), _ptr(row)))
 
 
 def psso_autotune(problems, precision=PSSO_PREC_F64, generations=200, **config):

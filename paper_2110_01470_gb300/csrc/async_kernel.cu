@@ -95,10 +95,10 @@ __device__ __forceinline__ void search(const Hot& in, const Pos* xr, const Pos* 
         const int nvalid = min(4, in.D - 4 * c);
         const uint32_t valid = (1u << nvalid) - 1u;
         if (g == 0) {
-            fresh_chunk(x[q], valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+            fresh_chunk(x[q], valid, (uint32_t)c, (uint32_t)i + in.i_base, 0u, TAG_INIT, in);
             continue;
         }
-        const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+        const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3r), in.k0, in.k1);
         Pos a[4], p[4], t[4];
         ld4_cg((in.order ? xr : gs) + 4 * c, a);
         ld4_cg(pr + 4 * c, p);
@@ -114,7 +114,7 @@ __device__ __forceinline__ void search(const Hot& in, const Pos* xr, const Pos* 
             if (!l3) nf |= 1u << m;
         }
         nf &= valid;
-        if (nf) fresh_chunk(x[q], nf, (uint32_t)c, (uint32_t)i, gg, TAG_FRESH, in);
+        if (nf) fresh_chunk(x[q], nf, (uint32_t)c, (uint32_t)i + in.i_base, gg, TAG_FRESH, in);
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             if (m >= nvalid) x[q][m] = Pos(0);

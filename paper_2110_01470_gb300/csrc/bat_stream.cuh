@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
                 const int nvalid = min(4, in.D - 4 * c);
                 const uint32_t valid = (1u << nvalid) - 1u;
                 if (g == 0) {
-                    fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+                    fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i + in.i_base, 0u, TAG_INIT, in);
                 } else {
                     // the slice's loads first: the draws below do not depend on
                     // them and cover their latency
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
                     ld4((in.order ? gs : xr) + 4 * c, xo);
                     ld4(prow + 4 * c, po);
                     ld4((in.order ? xr : gs) + 4 * c, go);
-                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3r), in.k0, in.k1);
                     uint4 fb = make_uint4(0u, 0u, 0u, 0u);
                     if (sizeof(Pos) == 4)
-                        fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+                        fb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3f), in.k0, in.k1);
                     uint32_t nf = 0;
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
                             for (int m = 0; m < 4; ++m)
                                 if (nf & (1u << m)) x[m] = (Pos)fresh_f32(word_of(fb, m), in);
                         } else {
-                            fresh_chunk(x, nf, (uint32_t)c, (uint32_t)i, gg, TAG_FRESH, in);
+                            fresh_chunk(x, nf, (uint32_t)c, (uint32_t)i + in.i_base, gg, TAG_FRESH, in);
                         }
                     }
 #pragma unroll

@@ -75,6 +75,7 @@ struct HostInst {
     size_t off_X = 0, off_P = 0, off_pf64 = 0, off_plo = 0, off_phi = 0, off_pver = 0,
            off_pflag = 0, off_grow = 0, off_rec = 0, off_rec2 = 0, off_gb = 0, off_gbrow = 0,
            off_log = 0, off_o64 = 0, off_o32 = 0, off_w64 = 0, off_w32 = 0, off_M64 = 0, off_M32 = 0;
+    int64_t i_base = 0;           // shard of a larger swarm: index of its first particle
     bool tc = false;              // generations run by the tensor-core pipeline
     bool bp = false;              // generations run by the batched throughput pipeline
     rot::RotHost rh{};
@@ -448,6 +449,7 @@ void fill_instdev(psso_ctx* h, std::vector<InstDev>& out)
         d.log = reinterpret_cast<LogDev*>(A + I.off_log);
         d.log_cap = h->cfg.log_stride > 0 ? h->cfg.log_capacity : 0;
         d.log_stride = h->cfg.log_stride;
+        d.i_base = (uint32_t)I.i_base;
         out[k] = d;
     }
 }
@@ -744,8 +746,37 @@ extern "C" {
 
 const char* psso_last_error(void) { return g_last_error.c_str(); }
 
+psso_status create_impl(const psso_problem* problems, int32_t count, const psso_config* cfg, int64_t i_base,
+                        psso_handle* out);
+
 psso_status psso_create_ex(const psso_problem* problems, int32_t count, const psso_config* cfg,
                            psso_handle* out)
+{
+    return create_impl(problems, count, cfg, 0, out);
+}
+
+psso_status psso_create_shard(const psso_problem* problem, int64_t first, int64_t count, const psso_config* cfg,
+                              psso_handle* out)
+{
+    if (!out) return fail(PSSO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!problem) return fail(PSSO_ERR_ARG, "problem is NULL");
+    if (first < 0 || count < 1 || first + count > problem->N || first + count > 0xffffffffLL)
+        return fail(PSSO_ERR_ARG, "psso_create_shard: need 0 <= first, 1 <= count, first + count <= N");
+    psso_config c{};
+    if (cfg) c = *cfg;
+    if (c.flow != PSSO_FLOW_SYNC)
+        return fail(PSSO_ERR_UNSUPPORTED, "psso_create_shard: the asynchronous flow cannot be split");
+    // the whole shard in one block: its gBest row is restored from the handle's
+    // gBest state at every launch, where psso_set_gbest puts the swarm's
+    c.single_block_max = 0x3fffffff;
+    psso_problem pr = *problem;
+    pr.N = count;
+    return create_impl(&pr, 1, &c, first, out);
+}
+
+psso_status create_impl(const psso_problem* problems, int32_t count, const psso_config* cfg, int64_t i_base,
+                        psso_handle* out)
 {
     const Range range("psso_create_ex");
     if (!out) return fail(PSSO_ERR_ARG, "out is NULL");
@@ -795,6 +826,7 @@ psso_status psso_create_ex(const psso_problem* problems, int32_t count, const ps
     for (int32_t k = 0; k < count; ++k) {
         HostInst& I = h->inst[k];
         I.pr = problems[k];
+        I.i_base = i_base;
         I.o.assign((size_t)I.pr.D, 0.0);
         if (I.pr.shift) std::copy(I.pr.shift, I.pr.shift + I.pr.D, I.o.begin());
         if (I.pr.weights) I.w.assign(I.pr.weights, I.pr.weights + I.pr.D);
@@ -1058,6 +1090,46 @@ psso_status psso_best(psso_handle h, int32_t instance, double* value, int64_t* i
     if (value) *value = gb.f64;
     if (index) *index = gb.idx;
     if (row) return copy_row(h, I, I.off_gbrow, 1, row);
+    return PSSO_OK;
+}
+
+psso_status psso_set_gbest(psso_handle h, int32_t instance, double value, int64_t index, const double* row)
+{
+    if (!h || !row) return fail(PSSO_ERR_ARG, "handle or row is NULL");
+    if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
+    if (!std::isfinite(value)) return fail(PSSO_ERR_ARG, "psso_set_gbest: value must be finite");
+    if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier");
+    const HostInst& I = h->inst[instance];
+    if (h->async || (!I.tc && !I.bp && I.R != 1))
+        return fail(PSSO_ERR_UNSUPPORTED,
+                    "psso_set_gbest: the instance's gBest comes from a cross-block exchange or the "
+                    "asynchronous flow (create it with psso_create_shard)");
+    const size_t D = (size_t)I.pr.D;
+    std::vector<char> buf((size_t)I.Dp * h->pos_size + sizeof(GBestDev), 0);
+    for (size_t j = 0; j < D; ++j) {
+        if (!(row[j] >= I.pr.lb && row[j] <= I.pr.ub))
+            return fail(PSSO_ERR_ARG, "psso_set_gbest: the row must lie inside [lb, ub]");
+        if (h->pos_size == 4) {
+            const float f = (float)row[j];
+            if ((double)f != row[j]) return fail(PSSO_ERR_ARG, "psso_set_gbest: F32 lattice rows hold floats");
+            reinterpret_cast<float*>(buf.data())[j] = f;
+        } else {
+            reinterpret_cast<double*>(buf.data())[j] = row[j];
+        }
+    }
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    GBestDev gb;
+    CUDA_TRY(cudaMemcpy(&gb, h->arena + I.off_gb, sizeof gb, cudaMemcpyDeviceToHost));
+    gb.idx = index;
+    gb.f64 = value;
+    gb.has64 = 1;
+    gb.lo = float_at_or_below(value);   // the largest float <= value
+    gb.hi = float_at_or_above(value);
+    gb.ver = 0xffffffffu;   // no local pBest row has this version: the row cache is refreshed
+    CUDA_TRY(cudaMemcpy(h->arena + I.off_gbrow, buf.data(), (size_t)I.Dp * h->pos_size, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->arena + I.off_gb, &gb, sizeof gb, cudaMemcpyHostToDevice));
+    h->h2d += (int64_t)((size_t)I.Dp * h->pos_size + sizeof gb);
     return PSSO_OK;
 }
 

@@ -113,7 +113,9 @@ struct InstDev {
     LogDev* log;
     int64_t log_cap;
     int32_t log_stride;
-    int32_t pad1;
+    uint32_t i_base;              // particle index of the first particle in the whole swarm
+                                  // (a shard of a swarm split over several GPUs; 0 otherwise):
+                                  // every draw is keyed by i_base + the local index
 };
 
 // A contiguous range of one instance's particles owned by one block.

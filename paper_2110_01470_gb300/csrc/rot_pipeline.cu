@@ -88,10 +88,10 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
         const uint32_t valid = (1u << nvalid) - 1u;
         float x[4] = {0.f, 0.f, 0.f, 0.f};
         if (g == 0) {
-            fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+            fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i + in.i_base, 0u, TAG_INIT, in);
         } else {
-            const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
-            const uint4 fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+            const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3r), in.k0, in.k1);
+            const uint4 fb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3f), in.k0, in.k1);
             float xo[4], po[4], go[4];
             // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
             // swaps them: keep x first, gBest third)

@@ -97,6 +97,7 @@ struct Hot {
     uint32_t tfull;               // bit 0/1/2: Tg/Tp/Tw equal 2^32 (always taken)
     uint32_t k0, k1, sid;
     uint32_t order;               // 1: Eq. 2.1 as printed (first interval keeps x, third takes gBest)
+    uint32_t i_base;              // draws are keyed by particle index i_base + local index
     float S32, L32, lbf, ubf;
     double lb, ub, span;
     const double* o64;
@@ -117,7 +118,7 @@ __device__ __forceinline__ Hot hot_of(const InstDev& d)
     h.Tw32 = d.Tw >= 0x100000000ULL ? 0xffffffffu : (uint32_t)d.Tw;
     h.tfull = (d.Tg >= 0x100000000ULL ? 1u : 0u) | (d.Tp >= 0x100000000ULL ? 2u : 0u) |
               (d.Tw >= 0x100000000ULL ? 4u : 0u);
-    h.k0 = d.k0; h.k1 = d.k1; h.sid = d.sid; h.order = d.order;
+    h.k0 = d.k0; h.k1 = d.k1; h.sid = d.sid; h.order = d.order; h.i_base = d.i_base;
     h.S32 = d.S32; h.L32 = d.L32; h.lbf = d.lbf; h.ubf = d.ubf;
     h.lb = d.lb; h.ub = d.ub; h.span = d.span;
     h.o64 = d.o64; h.o32 = d.o32; h.w64 = d.w64; h.w32 = d.w32;

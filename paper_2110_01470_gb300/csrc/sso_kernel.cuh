@@ -399,14 +399,14 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
             if (g == 0) {
 #pragma unroll
                 for (int m = 0; m < 4; ++m) s.x[q][m] = Pos(0);
-                fresh_chunk(s.x[q], valid, (uint32_t)c, (uint32_t)i, 0u, TAG_INIT, in);
+                fresh_chunk(s.x[q], valid, (uint32_t)c, (uint32_t)i + in.i_base, 0u, TAG_INIT, in);
             } else {
                 // rho block and (FP32 lattice) fresh block are independent: both
                 // are generated together so their latencies overlap.
-                const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3r), in.k0, in.k1);
+                const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3r), in.k0, in.k1);
                 uint4 fb = make_uint4(0u, 0u, 0u, 0u);
                 if (sizeof(Pos) == 4)
-                    fb = philox10(make_uint4((uint32_t)c, (uint32_t)i, gg, ctr3f), in.k0, in.k1);
+                    fb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3f), in.k0, in.k1);
                 Pos xo[4], po[4], go[4];
                 // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
                 // swaps them: keep x first, gBest third)
@@ -430,7 +430,7 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
                         for (int m = 0; m < 4; ++m)
                             if (nf & (1u << m)) s.x[q][m] = (Pos)fresh_f32(word_of(fb, m), in);
                     } else {
-                        fresh_chunk(s.x[q], nf, (uint32_t)c, (uint32_t)i, gg, TAG_FRESH, in);
+                        fresh_chunk(s.x[q], nf, (uint32_t)c, (uint32_t)i + in.i_base, gg, TAG_FRESH, in);
                     }
                 }
 #pragma unroll
