@@ -296,9 +296,11 @@ TRAFFIC = {
     ("rot_gemm_fit", "rotated_d1000"): ("", 56.755712e6 + 1.514752e6),
     ("sso_generations", "rastrigin_d100"): ("", None),
 }
+_COMMON = ["sso_common.cuh", "devmath.cuh", "psso_internal.h", "checked.cuh"]
 KERNEL_SOURCES = {
-    "rot_gemm_fit": ["tc_gemm.cuh", "rot_pipeline.cu", "sso_common.cuh", "devmath.cuh"],
-    "sso_generations": ["sso_kernel.cuh", "sso_common.cuh", "devmath.cuh", "gen_variant.cu"],
+    "rot_gemm_fit": ["tc_gemm.cuh", "rot_pipeline.cu", "rot_pipeline.h", *_COMMON],
+    "sso_generations": ["sso_kernel.cuh", "gen_variant.cu", *_COMMON],
+    "bat_stream": ["bat_stream.cuh", "sso_kernel.cuh", "gen_variant.cu", *_COMMON],
 }
 
 
@@ -379,7 +381,7 @@ def accept_rate(psso, problems, prec, t, sptr, stride=10):
         psso.psso_destroy(h)
 
 
-def batched_roofline(psso, problems, prec, t, sptr, live, gens=20):
+def batched_roofline(psso, problems, prec, t, sptr, live, workload, gens=20):
     """Batched pipeline: per-kernel event timing (psso_time_kernels) and the
     HBM roofline of the dominant step kernel.  Algorithmic bytes per update
     (FP32 positions): write x 4, read the selected source 2 (x with
@@ -422,7 +424,8 @@ def batched_roofline(psso, problems, prec, t, sptr, live, gens=20):
                         alu_ops_per_update(p, prec) * p["N"] * p["D"] / alu_rate)
                     for p, a in zip(problems, alpha))
     return {"bound": "hbm", "achieved": b_alg[dom] / t_dom / 1e9, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": b_alg[dom] / t_dom / hbm, "traffic": None,
+            "unit": "GB/s", "frac": b_alg[dom] / t_dom / hbm,
+            "traffic": traffic_of("bat_stream", workload) if dom == "stream" else None,
             "kernel": "bat_stream (batched step kernel, rows over 128 variables)" if dom == "stream"
                       else "bat_step (batched step kernel, rows up to 128 variables)",
             "kernel_ms_per_launch": ms[dom],
@@ -700,7 +703,7 @@ def main():
     kernel_s = (sum(kern_ms) / len(kern_ms)) / 1e3
     n_bat = st.get("batch_classes", 0)
     if n_bat and st["blocks"] == 0:
-        roofline = batched_roofline(psso, problems, prec, t, sptr, live)
+        roofline = batched_roofline(psso, problems, prec, t, sptr, live, args.workload)
     else:
         roofline = tensor_roofline(psso, problems, prec, sptr, args.workload)
     if roofline is None:

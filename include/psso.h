@@ -419,7 +419,9 @@ psso_status psso_fitness_backward_ws(psso_fn fn, int64_t N, int64_t D, const flo
  * one that does leaves the oracle's trajectory.  *improved (may be NULL) is
  * set to 1 when the row was replaced, else 0.  Synchronises the handle's
  * stream.  PSSO_ERR_ARG for a bad instance, steps < 0 or lr not a finite
- * value >= 0. */
+ * value >= 0; PSSO_ERR_UNSUPPORTED on a shard handle (its gBest may be
+ * another shard's particle); PSSO_ERR_STATE while the gBest is one that
+ * psso_set_gbest put there with an index outside the instance. */
 psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double lr, int32_t* improved);
 
 /* Rotation z = M (x - o) of N rows on the tensor cores (the transform of the
@@ -507,6 +509,21 @@ typedef struct {
  * if one ran out).  Takes well under a second; allocates 4 KiB for the call;
  * synchronises.  Changes no device setting. */
 psso_status psso_microbench(psso_peaks* out, void* stream);
+
+/* Index checks (a debugging build; the paper has no counterpart).  A library
+ * compiled with -DPSSO_CHECKED verifies, in every kernel, each index it
+ * computes into a buffer -- a particle's row, a unit's range and shared-memory
+ * window, an exchange slot, a log entry, a list slot -- before the access; a
+ * failed check records (site, index) of the first failure and skips the
+ * access (nothing traps).  psso_check_report waits for the device, then sets
+ * *site (0 = no failure; otherwise a site number, 2..15, naming the kind of
+ * index) and *index (the offending index); with clear != 0 the record is reset.
+ * psso_check_selftest enqueues, on `stream`, one failed check of site 1 with
+ * the given index and no memory access (it proves the record and report path).
+ * Both return PSSO_ERR_UNSUPPORTED in the default build, PSSO_ERR_ARG for a
+ * NULL pointer. */
+psso_status psso_check_report(int32_t* site, int64_t* index, int32_t clear);
+psso_status psso_check_selftest(int64_t index, void* stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* psso_last_error(void);

@@ -108,11 +108,14 @@ class psso_stats_t(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libpsso.so (raises if it has not been built)."""
+def load(path: str = None):
+    """Load libpsso.so (raises if it has not been built).  ``path`` (or the
+    environment variable PSSO_LIBRARY) selects another build of the same
+    sources, e.g. the index-checked copy of ``build_library(checked=True)``."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("PSSO_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with "
                            "`python -m paper_2110_01470_gb300.build` (needs nvcc)")
@@ -172,6 +175,9 @@ def load(path: str = LIB_PATH):
         "psso_create_shard": ([ctypes.POINTER(psso_problem), ctypes.c_int64, ctypes.c_int64,
                                ctypes.POINTER(psso_config), ctypes.POINTER(H)], st),
         "psso_set_gbest": ([H, ctypes.c_int32, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p], st),
+        "psso_check_report": ([ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.c_int32], st),
+        "psso_check_selftest": ([ctypes.c_int64, ctypes.c_void_p], st),
         "psso_last_error": ([], ctypes.c_char_p),
         "psso_destroy": ([H], None),
     }
@@ -492,6 +498,23 @@ def psso_microbench(stream=None):
     out = psso_peaks()
     _check(load().psso_microbench(ctypes.byref(out), stream))
     return {k: getattr(out, k) for k, _ in psso_peaks._fields_ if k != "reserved"}
+
+
+CHECK_SITES = {1: "selftest", 2: "unit range", 3: "unit shared memory", 4: "row", 5: "exchange slot",
+               6: "log entry", 7: "gBest source row", 8: "refined row", 9: "batched instance",
+               10: "batched row", 11: "list slot", 12: "tensor-pipeline row", 13: "evaluated row",
+               14: "asynchronous-flow row", 15: "GEMM tile"}
+
+
+def psso_check_report(clear=False):
+    """First failed index check of a checked build: (site, index), site 0 if none."""
+    site, index = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(load().psso_check_report(ctypes.byref(site), ctypes.byref(index), 1 if clear else 0))
+    return site.value, index.value
+
+
+def psso_check_selftest(index, stream=None):
+    _check(load().psso_check_selftest(int(index), stream))
 
 
 def psso_last_error():

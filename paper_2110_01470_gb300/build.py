@@ -9,6 +9,10 @@ into one shared library next to this file.  Usage:
 the same sources compiled with ``-DPSSO_TRACE`` (the persistent kernel then
 stamps ``%globaltimer`` at its phase boundaries, see ``trace_generations``)
 into ``_build/libpsso_trace.so``; the package's own library is untouched.
+``build_library(checked=True)`` (or ``--checked``) builds the index-checked
+copy ``_build/libpsso_checked.so`` (``-DPSSO_CHECKED``: every kernel verifies
+the indices it computes before the access and records the first failure,
+read back with ``psso_check_report``).
 """
 from __future__ import annotations
 
@@ -45,14 +49,20 @@ def _newest_input() -> float:
 
 TRACE_OBJDIR = os.path.join(ROOT, "_build", "trace")
 TRACE_LIB = os.path.join(ROOT, "_build", "libpsso_trace.so")
+CHECKED_OBJDIR = os.path.join(ROOT, "_build", "checked")
+CHECKED_LIB = os.path.join(ROOT, "_build", "libpsso_checked.so")
 
 
-def build_library(force: bool = False, verbose: bool = False, trace: bool = False) -> str:
+def build_library(force: bool = False, verbose: bool = False, trace: bool = False,
+                  checked: bool = False) -> str:
     """Compile and link libpsso.so if any source is newer than it (with
-    ``trace``: the phase-stamped profiling copy in ``_build/``)."""
-    lib = TRACE_LIB if trace else LIB
-    objdir = TRACE_OBJDIR if trace else OBJDIR
-    flags = NVCC_FLAGS + (["-DPSSO_TRACE"] if trace else [])
+    ``trace``: the phase-stamped profiling copy in ``_build/``; with
+    ``checked``: the index-checked copy in ``_build/``)."""
+    if trace and checked:
+        raise ValueError("build either the traced or the checked copy")
+    lib = TRACE_LIB if trace else CHECKED_LIB if checked else LIB
+    objdir = TRACE_OBJDIR if trace else CHECKED_OBJDIR if checked else OBJDIR
+    flags = NVCC_FLAGS + (["-DPSSO_TRACE"] if trace else []) + (["-DPSSO_CHECKED"] if checked else [])
     if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
         return lib
     os.makedirs(objdir, exist_ok=True)
@@ -97,4 +107,5 @@ def build_library(force: bool = False, verbose: bool = False, trace: bool = Fals
 
 
 if __name__ == "__main__":
-    print(build_library(force="--force" in sys.argv, verbose=True, trace="--trace" in sys.argv))
+    print(build_library(force="--force" in sys.argv, verbose=True, trace="--trace" in sys.argv,
+                        checked="--checked" in sys.argv))

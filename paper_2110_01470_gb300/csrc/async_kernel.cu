@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(256) sso_async(const AsyncParams p)
     if (p.g_begin > 0) {
         b = __ldcg(&d.gb->idx);
         gF = __ldcg(&d.gb->f64);
+        if (!PSSO_CHK(b >= 0 && b < N, CHK_ASYNC_ROW, b)) return;   // the same in every block
     }
     unsigned rc = 0;   // rounds so far in this launch (selects the `first` slot)
     for (int64_t g = p.g_begin; g <= p.g_end; ++g) {
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(256) sso_async(const AsyncParams p)
             if (threadIdx.x == 0) s_k = ld_volatile_u32(&c->first[slot]);
             __syncthreads();
             const unsigned k = s_k;
+            if (!PSSO_CHK(k == NONE || (int64_t)k < N, CHK_ASYNC_ROW, k)) return;   // the same in every block
             const int64_t last = (k == NONE) ? N - 1 : (int64_t)k;
             // commit s..last: position, and pBest when strictly better (Alg. 1)
             for (int64_t i = s + gr.gid; i <= last; i += gr.ngroups) {

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
         const int k = __ldg(p.ids + lo);
         const int64_t i = gid - __ldg(p.first + lo);
         const InstDev& d = p.inst[k];
+        if (!PSSO_CHK(i >= 0 && i < d.N, CHK_BAT_ROW, gid)) continue;
         const Hot in = hot_of(d);
         const int fn = in.fn;
         const int nq = (in.nchunks + 31) >> 5;

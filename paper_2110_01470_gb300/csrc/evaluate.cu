@@ -29,6 +29,7 @@ __global__ void evaluate_rows(const InstDev in, const void* X, int64_t N, double
 {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= N) return;
+    if (!PSSO_CHK(in.maxc * 128 >= in.D, CHK_EVAL_ROW, in.D)) return;
     const Hot h = hot_of(in);
     if constexpr (F32) {
         const float* r = static_cast<const float*>(X) + row * in.Dp;

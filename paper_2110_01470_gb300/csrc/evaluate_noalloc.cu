@@ -130,6 +130,7 @@ __global__ void eval_noalloc(const Hot in, const double* X, int64_t N, double* f
 {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= N) return;
+    if (!PSSO_CHK(in.maxc * 128 >= in.D, CHK_EVAL_ROW, in.D)) return;
     const double* xr = X + row * in.D;
     double* e = err ? err + row : nullptr;
     switch (in.maxc) {

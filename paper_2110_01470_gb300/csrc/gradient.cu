@@ -211,6 +211,7 @@ __global__ void fitness_fb(const Hot in, const float* X, int64_t N, const float*
 {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= N) return;
+    if (!PSSO_CHK(in.maxc * 128 >= in.D, CHK_EVAL_ROW, in.D)) return;
     const float* xr = X + row * in.D;
     const float gfr = BWD ? gf[row] : 0.f;
     float* fo = BWD ? nullptr : f + row;
@@ -266,6 +267,7 @@ __device__ void polish_row(const InstDev& in, int owner_rank, int64_t g, int ste
     const double fnew = fit64<Pos, MAXC>(hin, xp, lane, 0xffffffffu, 32);
     if (!(fnew < fold)) return;
     const int64_t b = in.gb->idx;
+    if (!PSSO_CHK(b >= 0 && b < in.N && owner_rank < in.R, CHK_GBEST_SRC, b)) return;
     Pos* prow = static_cast<Pos*>(in.P) + b * in.Dp;
     Pos* gw = static_cast<Pos*>(in.gbrow);
 #pragma unroll

@@ -130,6 +130,7 @@ struct psso_ctx {
     bool failed = false;
     // asynchronous flow (Alg. 1): one cooperative kernel; its scratch and control words
     bool async = false;
+    bool shard = false;           // created by psso_create_shard
     void* amem = nullptr;
     AsyncCtl* actl = nullptr;
     void* axs = nullptr;
@@ -742,6 +743,19 @@ psso_status read_status(psso_ctx* h)
 }  // namespace
 
 // ---------------------------------------------------------------------------
+#ifdef PSSO_CHECKED
+namespace {
+std::vector<chk::Reader>& checked_readers()
+{
+    static std::vector<chk::Reader> v;   // filled while the library loads (static initialisers)
+    return v;
+}
+// A failed check with no memory access: proves the record and report path.
+__global__ void check_selftest_kernel(long long index) { (void)PSSO_CHK(false, CHK_SELFTEST, index); }
+}  // namespace
+void psso::chk::add_reader(Reader r) { checked_readers().push_back(r); }
+#endif
+
 extern "C" {
 
 const char* psso_last_error(void) { return g_last_error.c_str(); }
@@ -772,7 +786,9 @@ psso_status psso_create_shard(const psso_problem* problem, int64_t first, int64_
     c.single_block_max = 0x3fffffff;
     psso_problem pr = *problem;
     pr.N = count;
-    return create_impl(&pr, 1, &c, first, out);
+    const psso_status st = create_impl(&pr, 1, &c, first, out);
+    if (st == PSSO_OK) (*out)->shard = true;
+    return st;
 }
 
 psso_status create_impl(const psso_problem* problems, int32_t count, const psso_config* cfg, int64_t i_base,
@@ -1225,11 +1241,18 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
     if (instance < 0 || instance >= (int32_t)h->inst.size()) return fail(PSSO_ERR_ARG, "instance out of range");
     if (steps < 0 || !(lr >= 0.0) || !std::isfinite(lr)) return fail(PSSO_ERR_ARG, "need steps >= 0 and a finite lr >= 0");
     if (h->failed) return fail(PSSO_ERR_STATE, "the handle failed earlier");
+    if (h->shard)
+        return fail(PSSO_ERR_UNSUPPORTED,
+                    "psso_polish: a shard's gBest may be another shard's particle (polish the swarm's "
+                    "gBest on its owner and pass the result with psso_set_gbest)");
     psso_status st = read_status(h);
     if (st != PSSO_OK) return st;
     const HostInst& I = h->inst[instance];
     GBestDev before;
     CUDA_TRY(cudaMemcpy(&before, h->arena + I.off_gb, sizeof before, cudaMemcpyDeviceToHost));
+    if (before.idx < 0 || before.idx >= I.pr.N)
+        return fail(PSSO_ERR_STATE, "psso_polish: the gBest index (set by psso_set_gbest) names no particle "
+                                    "of this instance; run a generation first");
     int owner = -1;
     if (I.R > 1)
         for (const auto& u : h->units)
@@ -1393,6 +1416,45 @@ void psso_destroy(psso_handle h)
     if (h->bat.mem) cudaFree(h->bat.mem);
     if (h->amem) cudaFree(h->amem);
     delete h;
+}
+
+
+// Index checks of the checked build: the first failure any kernel recorded.
+psso_status psso_check_report(int32_t* site, int64_t* index, int32_t clear)
+{
+    if (!site || !index) return fail(PSSO_ERR_ARG, "psso_check_report: site and index must not be NULL");
+    *site = 0;
+    *index = 0;
+#ifndef PSSO_CHECKED
+    (void)clear;
+    return fail(PSSO_ERR_UNSUPPORTED, "psso_check_report: not a checked build (compile with -DPSSO_CHECKED)");
+#else
+    CUDA_TRY(cudaDeviceSynchronize());
+    unsigned long long first = 0;
+    for (chk::Reader r : checked_readers()) {
+        unsigned long long v = 0;
+        CUDA_TRY(r(&v, clear != 0));
+        if (!first) first = v;
+    }
+    if (first) {
+        *site = (int32_t)(first >> 48);
+        *index = (int64_t)(first << 16) >> 16;   // the 48-bit index, sign-extended
+    }
+    return PSSO_OK;
+#endif
+}
+
+psso_status psso_check_selftest(int64_t index, void* stream)
+{
+#ifndef PSSO_CHECKED
+    (void)index;
+    (void)stream;
+    return fail(PSSO_ERR_UNSUPPORTED, "psso_check_selftest: not a checked build (compile with -DPSSO_CHECKED)");
+#else
+    check_selftest_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>((long long)index);
+    CUDA_TRY(cudaGetLastError());
+    return PSSO_OK;
+#endif
 }
 
 }  // extern "C"

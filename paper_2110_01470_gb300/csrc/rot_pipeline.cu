@@ -50,6 +50,13 @@
 namespace psso {
 namespace rot {
 
+// Appends v to a list of capacity cap (the counter may live in shared memory).
+__device__ __forceinline__ void list_push(int32_t* list, unsigned* count, long long cap, int32_t v)
+{
+    const unsigned slot = atomicAdd(count, 1u);
+    if (PSSO_CHK((long long)slot < cap, CHK_LIST, slot)) list[slot] = v;
+}
+
 using tc::BM;
 using tc::BN;
 
@@ -208,7 +215,8 @@ struct FitEpi {
         rQ = __fadd_rn(rQ, eq);
         if (c == BN / 32 - 1) {
             const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
-            if (i < r->N) r->part[i * r->nJt + blockIdx.y] = make_float4(acc, acc2, accE, rQ);
+            if (i < r->N && PSSO_CHK(blockIdx.y < (unsigned)r->nJt, CHK_TILE, blockIdx.y))
+                r->part[i * r->nJt + blockIdx.y] = make_float4(acc, acc2, accE, rQ);
         }
     }
 };
@@ -301,7 +309,7 @@ __global__ void rot_decide(const RotDev r)
             }
         }
         if (lane == 0) {
-            if (undecided) r.list1[atomicAdd(&r.ctl->n1, 1u)] = (int32_t)i;
+            if (undecided) list_push(r.list1, &r.ctl->n1, r.N, (int32_t)i);
             if (accept) atomicAdd(&blk_acc, 1ull);
         }
     }
@@ -324,6 +332,7 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
     const InstDev& d = *r.inst;
     const unsigned n = r.ctl->n1;
     const int D = r.D;
+    if (!PSSO_CHK(n <= r.N && D <= 1024, CHK_LIST, n)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nJb = (D + 127) / 128;
     const float U = 0x1p-24f;
@@ -337,6 +346,7 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
         const int32_t i = r.list1[e];
+        if (!PSSO_CHK(i >= 0 && i < r.N, CHK_ROT_ROW, i)) continue;
         if (row == 1 && (d.pflag[i] & 1u)) continue;     // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
         __syncthreads();
@@ -423,6 +433,7 @@ template <int MAXC>
 __device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int lane)
 {
     const int32_t i = r.list1[e];
+    if (!PSSO_CHK(i >= 0 && i < r.N, CHK_ROT_ROW, i)) return;
     const int64_t g = r.ctl->gen;
     const size_t ox = (size_t)(2 * e) * d.Dp, op = ox + d.Dp;
     float plo = d.plo[i], phi = d.phi[i];
@@ -456,7 +467,7 @@ __device__ void fix32_one(const RotDev& r, const InstDev& d, long long e, int la
         } else {
             d.plo[i] = plo;
             d.phi[i] = phi;
-            if (!reject) r.list3[atomicAdd(&r.ctl->n3, 1u)] = i;
+            if (!reject) list_push(r.list3, &r.ctl->n3, r.N, i);
         }
         atomicAdd(&r.ctl->refined, have_p ? 1ull : 2ull);
     }
@@ -467,6 +478,7 @@ __global__ void rot_fix32(const RotDev r)
     const int lane = threadIdx.x & 31;
     const InstDev& d = *r.inst;
     const unsigned n = r.ctl->n1;
+    if (!PSSO_CHK(n <= r.N, CHK_LIST, n)) return;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < (long long)n;
          e += nwarps) {
@@ -499,6 +511,7 @@ __global__ void rot_z64(const RotDev r, int which)
     const InstDev& d = *r.inst;
     const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;   // which 2 or 4: list 2
     const int D = r.D;
+    if (!PSSO_CHK(n <= r.N && D <= 1024, CHK_LIST, n)) return;
     const int nJb = (D + 127) / 128;
     const long long items = (long long)n * 2 * nJb;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
@@ -506,6 +519,7 @@ __global__ void rot_z64(const RotDev r, int which)
         const int row = (int)((it / nJb) & 1);
         const long long e = it / nJb / 2;
         const int32_t i = which == 1 ? r.list3[e] : r.list2[e];
+        if (!PSSO_CHK(i >= 0 && i < r.N, CHK_ROT_ROW, i)) continue;
         const bool needed = which == 1 ? (row == 0 || !(d.pflag[i] & 1u)) : row == 1;
         if (!needed) continue;          // uniform over the block
         const float* src = static_cast<const float*>(row == 0 ? d.X : d.P) + (int64_t)i * d.Dp;
@@ -536,6 +550,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
     const double* zp = zx + d.Dp;
     if (which == 1) {
         const int32_t i = r.list3[e];
+        if (!PSSO_CHK(i >= 0 && i < r.N, CHK_ROT_ROW, i)) return;
         const bool have_p = (d.pflag[i] & 1u) != 0;
         const double fx = fit64_row<double>(hz, zx, false);
         const double fp = have_p ? d.pf64[i] : fit64_row<double>(hz, zp, false);
@@ -561,6 +576,7 @@ __device__ void fix_one(const RotDev& r, const InstDev& d, int which, long long 
         }
     } else {   // list 2 (which 2: in a generation; 4: on demand, outside the counters)
         const int32_t i = r.list2[e];
+        if (!PSSO_CHK(i >= 0 && i < r.N, CHK_ROT_ROW, i)) return;
         const double fp = fit64_row<double>(hz, zp, false);
         if (lane == 0) {
             d.pf64[i] = fp;
@@ -577,6 +593,7 @@ __global__ void rot_fix(const RotDev r, int which)
     const int lane = threadIdx.x & 31;
     const InstDev& d = *r.inst;
     const unsigned n = which == 1 ? r.ctl->n3 : r.ctl->n2;
+    if (!PSSO_CHK(n <= r.N, CHK_LIST, n)) return;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < (long long)n;
          e += nwarps)
@@ -623,7 +640,7 @@ __global__ void __launch_bounds__(1024) rot_argmin(const RotDev r, int phase)
         if (threadIdx.x == 0) n2 = 0;
         __syncthreads();
         for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
-            if (d.plo[i] <= b.mh && !(d.pflag[i] & 1u)) r.list2[atomicAdd(&n2, 1u)] = (int32_t)i;
+            if (d.plo[i] <= b.mh && !(d.pflag[i] & 1u)) list_push(r.list2, &n2, r.N, (int32_t)i);
         __syncthreads();
         if (threadIdx.x == 0) {
             ctl->amb = 1;
@@ -691,7 +708,7 @@ __global__ void list_wide(const RotDev r)
     const InstDev& d = *r.inst;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
         if (!(d.pflag[i] & 1u) && too_wide(r.fn, d.plo[i], d.phi[i]))
-            r.list2[atomicAdd(&r.ctl->n2, 1u)] = (int32_t)i;
+            list_push(r.list2, &r.ctl->n2, r.N, (int32_t)i);
 }
 
 __global__ void clear_n2(RotCtl* ctl) { ctl->n2 = 0; }

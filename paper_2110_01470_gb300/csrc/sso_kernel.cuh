@@ -151,6 +151,7 @@ struct View {
     uint32_t* pver;
     uint32_t* pflag;
     int64_t base;       // particle i is entry i - base
+    int64_t n;          // entries (index checks of the checked build)
 };
 
 template <class Pos>
@@ -175,6 +176,7 @@ __device__ __forceinline__ View<Pos> make_view(const InstDev& in, const UnitDev&
         s += res_align((size_t)n * 4);
         v.pflag = reinterpret_cast<uint32_t*>(s);
         v.base = un.i0;
+        v.n = n;
     } else {
         v.X = static_cast<Pos*>(in.X);
         v.P = static_cast<Pos*>(in.P);
@@ -184,8 +186,25 @@ __device__ __forceinline__ View<Pos> make_view(const InstDev& in, const UnitDev&
         v.pver = in.pver;
         v.pflag = in.pflag;
         v.base = 0;
+        v.n = in.N;
     }
     return v;
+}
+
+// Checked build: a unit's particle range, rank and shared-memory windows.
+template <class Pos>
+__device__ __forceinline__ bool unit_checked(const InstDev& in, const UnitDev& un)
+{
+    const size_t dyn = dynamic_smem_bytes();
+    bool ok = PSSO_CHK(un.i0 >= 0 && un.i0 <= un.i1 && un.i1 <= in.N && un.rank >= 0 && un.rank < in.R,
+                       CHK_UNIT, un.i0);
+    ok = ok && PSSO_CHK(un.smem_off >= 0 && (size_t)un.smem_off + (size_t)in.Dp * sizeof(Pos) <= dyn,
+                        CHK_UNIT_SMEM, un.smem_off);
+    if (un.resident)
+        ok = ok && PSSO_CHK(un.res_off >= 0 &&
+                                (size_t)un.res_off + resident_bytes(un.i1 - un.i0, in.Dp, sizeof(Pos)) <= dyn,
+                            CHK_UNIT_SMEM, un.res_off);
+    return ok;
 }
 
 // Copies a resident unit between global memory and shared memory.
@@ -385,6 +404,15 @@ __device__ __forceinline__ void particle_compute(const Hot& in, const View<Pos>&
                                                  int64_t g, int lane_g, unsigned gmask,
                                                  PartState<Pos, MAXC>& s)
 {
+    if (!PSSO_CHK(e >= 0 && e < v.n, CHK_ROW, e)) {
+        s.accept = s.wstate = s.cachep = s.undecided = false;
+        s.rck = 0;
+        s.has64 = 0;
+        s.ver = 0;
+        s.f64v = s.cachef = DBL_MAX;
+        s.lo = s.hi = FLT_MAX;
+        return;
+    }
     const Pos* xr = v.X + e * in.Dp;
     const Pos* pr = v.P + e * in.Dp;
     const uint32_t gg = (uint32_t)g;
@@ -544,6 +572,7 @@ __device__ __forceinline__ void particle_commit(const Hot& in, const View<Pos>& 
                                                 PartState<Pos, MAXC>& s, unsigned long long& n_acc,
                                                 unsigned long long& n_rck)
 {
+    if (!PSSO_CHK(e >= 0 && e < v.n, CHK_ROW, e)) return;
     Pos* xr = v.X + e * in.Dp;
     Pos* pr = v.P + e * in.Dp;
 #pragma unroll
@@ -685,7 +714,9 @@ __device__ inline void write_gbest(const InstDev& in, const Winner& w, int64_t g
     gb->ver = w.ver;
     gb->has64 = w.has64;
     if (in.log_stride > 0 && in.log_cap > 0 && (g % in.log_stride) == 0) {
-        LogDev* e = in.log + ((g / in.log_stride) % in.log_cap);
+        const int64_t le = (g / in.log_stride) % in.log_cap;
+        if (!PSSO_CHK(le >= 0 && le < in.log_cap, CHK_LOG, le)) return;
+        LogDev* e = in.log + le;
         e->gen = g;
         e->idx = w.idx;
         e->value = w.has64 ? w.f64 : __longlong_as_double(0x7ff8000000000000LL);
@@ -710,7 +741,8 @@ __device__ __noinline__ Cand step_c_exact(const InstDev& in, const UnitDev un, c
     for (int64_t base = 0; base < n; base += 32) {
         const int64_t k = base + lane;
         const int64_t e = un.i0 + k - v.base;
-        const bool need = k < n && v.plo[e] <= m && !(v.pflag[e] & 1u);
+        const bool need = k < n && PSSO_CHK(e >= 0 && e < v.n, CHK_REFINE, e) && v.plo[e] <= m &&
+                          !(v.pflag[e] & 1u);
         unsigned bm = __ballot_sync(0xffffffffu, need);
         while (bm) {
             const int l = __ffs(bm) - 1;
@@ -732,7 +764,7 @@ __device__ __noinline__ Cand step_c_exact(const InstDev& in, const UnitDev un, c
     Cand ex = cand_none();
     for (int64_t k = lane; k < n; k += 32) {
         const int64_t e = un.i0 + k - v.base;
-        if (v.pflag[e] & 1u) {
+        if (PSSO_CHK(e >= 0 && e < v.n, CHK_REFINE, e) && (v.pflag[e] & 1u)) {
             Cand q = cand_none();
             q.v = v.pf64[e];
             q.i = (long long)(un.i0 + k);
@@ -1039,7 +1071,8 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
         Winner me;
         ok = read_record(recs + (size_t)un.rank * REC_WORDS, tag, me, p, un);
         if (__any_sync(0xffffffffu, !ok)) { if (lane == 0) sh.flag = 1; return; }
-        if (me.lo <= m && !me.has64) {
+        if (me.lo <= m && !me.has64 &&
+            PSSO_CHK(me.idx - v.base >= 0 && me.idx - v.base < v.n, CHK_REFINE, me.idx)) {
             const double f = fit64_row<Pos>(hot_of(in), v.P + (me.idx - v.base) * in.Dp, false);
             if (lane == 0) {
                 Winner ww = me;
@@ -1081,7 +1114,10 @@ __device__ __noinline__ void step_a(const KParams& p, const InstDev& in, const U
 
     // Fetch the winner's row if it is not the one already in shared memory.
     const bool changed = (sh.idx[uslot] != win.i) || (sh.ver[uslot] != win.ver);
-    if (changed) {
+    if (changed && !PSSO_CHK(win.rank >= 0 && win.rank < R, CHK_SLOT, win.rank)) {
+        if (lane == 0) give_up(p, un);
+        ok = false;
+    } else if (changed) {
         const uint64_t* src = static_cast<const uint64_t*>(in.grow) +
                               ((size_t)slot_of(gp) * R + win.rank) * (size_t)in.Dp * WPE;
         for (int ch = lane; ch < in.nchunks; ch += 32) {
@@ -1137,6 +1173,7 @@ __device__ __forceinline__ void step_d_publish(const KParams& p, const InstDev& 
     const int R = in.R;
     const uint32_t tag = (uint32_t)g;
     uint64_t* dst = static_cast<uint64_t*>(in.grow) + ((size_t)slot_of(g) * R + un.rank) * (size_t)in.Dp * WPE;
+    if (!PSSO_CHK(w.idx - v.base >= 0 && w.idx - v.base < v.n, CHK_GBEST_SRC, w.idx)) return;
     const Pos* src = v.P + (w.idx - v.base) * in.Dp;
     for (int ch = lane; ch < in.nchunks; ch += 32) {
         Pos t[4];
@@ -1163,7 +1200,7 @@ __device__ __noinline__ void step_d_local(const InstDev& in, const View<Pos>& v,
 {
     const int lane = threadIdx.x & 31;
     const bool changed = (sh.idx[uslot] != w.idx) || (sh.ver[uslot] != w.ver);
-    if (changed) {
+    if (changed && PSSO_CHK(w.idx - v.base >= 0 && w.idx - v.base < v.n, CHK_GBEST_SRC, w.idx)) {
         const Pos* src = v.P + (w.idx - v.base) * in.Dp;
         Pos* dst = static_cast<Pos*>(in.gbrow);
         for (int ch = lane; ch < in.nchunks; ch += 32) {
@@ -1396,6 +1433,10 @@ __global__ void __launch_bounds__(GenBound<MC>::threads) sso_generations(const K
     for (int u = u0; u < u1; ++u) {
         const UnitDev un = p.units[u];
         const InstDev& in = p.inst[un.inst];
+        if (!unit_checked<Pos>(in, un)) {
+            if (threadIdx.x == 0) { sh.flag = 1; give_up(p, un); }
+            break;
+        }
         Pos* gs = reinterpret_cast<Pos*>(smem + un.smem_off);
         const int slot = u - u0;
         if (un.resident && p.g_begin > 0) move_resident<Pos, F32R>(in, un, smem, true);
@@ -1413,6 +1454,9 @@ __global__ void __launch_bounds__(GenBound<MC>::threads) sso_generations(const K
         }
     }
     __syncthreads();
+#ifdef PSSO_CHECKED
+    if (sh.flag) return;
+#endif
 
     if (u1 - u0 == 1 && p.units[u0].pipelined) {
         const UnitDev un = p.units[u0];
@@ -1592,6 +1636,7 @@ __global__ void __launch_bounds__(256, BatBound<MC>::min_blocks) bat_step(const 
             }
             ent_end = __ldg(p.first + lo + 1);
         }
+        if (!PSSO_CHK(lo >= 0 && lo < p.n_ids, CHK_BAT_INST, gid)) break;
         const int k = __ldg(p.ids + lo);
         const int64_t i = gid - __ldg(p.first + lo);
         const InstDev& d = p.inst[k];
@@ -1605,6 +1650,7 @@ __global__ void __launch_bounds__(256, BatBound<MC>::min_blocks) bat_step(const 
         v.pver = d.pver;
         v.pflag = d.pflag;
         v.base = 0;
+        v.n = d.N;
         unsigned long long n_acc = 0, n_rck = 0;
         PartState<Pos, MC> st;
         particle_compute<Pos, F32R, MC>(in, v, static_cast<const Pos*>(d.gbrow), i, i, g, lane_g, gmask, st);

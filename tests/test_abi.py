@@ -121,3 +121,15 @@ def test_entry_points_fail_cleanly_without_gpu(libpath):
         psso.psso_run(None, 1)
     with pytest.raises(psso.PssoError):
         psso.psso_autotune([p], "f64", generations=1)
+
+
+def test_check_entry_points_unsupported_in_default_build(libpath):
+    """The index-check calls exist in every build; the default build answers
+    PSSO_ERR_UNSUPPORTED without touching the device."""
+    import paper_2110_01470_gb300 as psso
+    psso.load(libpath)
+    for call in (lambda: psso.psso_check_report(), lambda: psso.psso_check_selftest(5)):
+        with pytest.raises(psso.PssoError) as e:
+            call()
+        assert e.value.status == psso.PSSO_ERR_UNSUPPORTED
+        assert "checked build" in psso.psso_last_error()

@@ -69,3 +69,30 @@ def test_set_gbest_rejects_what_it_cannot_place(lib):
     with pytest.raises(lib.PssoError) as e:
         lib.psso_create_shard(p, 1990, 20)                      # past the swarm's end
     assert e.value.status == lib.PSSO_ERR_ARG
+
+
+def test_polish_refused_where_the_gbest_is_not_local(lib):
+    """A shard's gBest may be another shard's particle: psso_polish refuses
+    shard handles.  On a single-block handle whose gBest psso_set_gbest gave
+    an index outside the instance, it refuses until a generation has run."""
+    p = workload.problem("sphere", 200, 8, seed=2)
+    s = lib.psso_create_shard(p, 100, 100)
+    try:
+        lib.psso_run(s, 2)
+        with pytest.raises(lib.PssoError) as e:
+            lib.psso_polish(s, 0, steps=2, lr=1e-3)
+        assert e.value.status == lib.PSSO_ERR_UNSUPPORTED
+    finally:
+        lib.psso_destroy(s)
+    q = workload.problem("sphere", 100, 8, seed=2)
+    h = lib.psso_create_ex([q], single_block_max=1 << 20)      # one block
+    try:
+        lib.psso_run(h, 2)
+        lib.psso_set_gbest(h, 0, 0.5, 150, np.zeros(8))      # an index this instance does not hold
+        with pytest.raises(lib.PssoError) as e:
+            lib.psso_polish(h, 0, steps=2, lr=1e-3)
+        assert e.value.status == lib.PSSO_ERR_STATE
+        lib.psso_run(h, 1)                                   # the gBest is a local particle again
+        lib.psso_polish(h, 0, steps=2, lr=1e-3)
+    finally:
+        lib.psso_destroy(h)
