@@ -394,8 +394,8 @@ psso_status psso_fitness_backward(psso_fn fn, int64_t N, int64_t D, const float*
  * cores: z = M (x - o) for all N rows as one split-BF16 tcgen05 GEMM
  * (Z = (X - O) M^T), the function and its z-gradient per row from Z, and
  * the backward product M^T df/dz as a second GEMM (grad_X = G M, G the rows
- * grad_f[i] df/dz).  Each GEMM output carries a relative error of about
- * 2^-22 of sum |A_ik| |B_jk|.  `workspace` is caller-owned DEVICE memory,
+ * grad_f[i] df/dz).  Each GEMM output carries an error of at most about
+ * 2^-20 per MMA of sum |A_ik| |B_jk| (typically far less).  `workspace` is caller-owned DEVICE memory,
  * 256-byte aligned, of at least psso_fitness_workspace_size bytes; the calls
  * allocate nothing, enqueue on `stream` and return without waiting.  Unrotated
  * functions (and D < 16) need no workspace and run psso_fitness_forward /
@@ -433,9 +433,10 @@ psso_status psso_polish(psso_handle h, int32_t instance, int32_t steps, double l
  * in three accumulators over K blocks dealt round robin, the corrections in a
  * fourth) and added.  Error model:
  * |z~_j - sum_k M_jk d_k| <= c(Kp) * sum_k |M_jk| |d_k| + 2^-24 |z~_j|,
- * Kp = D rounded up to 64, c(Kp) = 1.05 (2^-22 1.04 (4 ceil(Kp/192)
+ * Kp = D rounded up to 64, c(Kp) = 1.05 (2^-20 1.04 (4 ceil(Kp/192)
  * + 5 (Kp/16) 2^-7) + 1.03 2^-23 + 5.12 2^-24) when every MMA instruction
- * errs by at most 2^-22 of its operand magnitudes.  1 <= N <= 2^24, 1 <= D <= 8192.  Allocates its
+ * errs by at most 2^-20 of its operand magnitudes (the probed accumulation
+ * of sm_103a errs by at most 0.625 2^-20).  1 <= N <= 2^24, 1 <= D <= 8192.  Allocates its
  * operand planes for the call and synchronises `stream`.  PSSO_ERR_TIMEOUT if
  * a pipeline wait ran out (the device is left usable). */
 psso_status psso_rotate(int64_t N, int64_t D, const float* X, const float* shift, const float* rotation,

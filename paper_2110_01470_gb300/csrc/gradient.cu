@@ -347,8 +347,8 @@ cudaError_t launch_polish(const InstDev* inst, int k, int lattice, int owner_ran
 //   backward  G_i = grad_f_i df/dz   from Z (same kernel, its z-gradient)
 //             grad_X = G M           second GEMM, B operand = the planes of M^T
 // Both GEMMs run the six split products of tc_gemm.cuh with FP32
-// accumulation: each output carries a relative error of about 2^-22 of
-// sum |A_ik| |B_jk|, far inside the gradient's own FP32 rounding.
+// accumulation: each output carries an error below 2^-20 per MMA of
+// sum |A_ik| |B_jk| (tc_gemm.cuh), typically far less.
 namespace gtc {
 
 using tc::BM;

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 def c_of(Kp):
     nkb = Kp // 64
     n0, n1 = 4 * ((nkb + 2) // 3), 5 * (Kp // 16)
-    return 1.05 * (2.0 ** -22 * 1.04 * (n0 + n1 * 2.0 ** -7) + 1.03 * 2.0 ** -23 + 2.02 * 2.0 ** -24
+    return 1.05 * (2.0 ** -20 * 1.04 * (n0 + n1 * 2.0 ** -7) + 1.03 * 2.0 ** -23 + 2.02 * 2.0 ** -24
                    + 3.1 * 2.0 ** -24)
 
 
