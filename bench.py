@@ -331,7 +331,8 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
     """Rotated swarms on the tensor-core pipeline: per-kernel event timing of
     the first such instance (psso_time_kernels) and the roofline of the GEMM
     kernel.  Algorithmic work is z = M (x - o): 2 N D^2 flops per generation;
-    the kernel executes six BF16 products over the padded extents."""
+    the kernel executes ten BF16 slice products (four 6-bit integer slices per
+    operand, weights 0..3) over the padded extents."""
     rot = [p for p in problems if p["fn"].startswith("rot_") and p["N"] >= 128 and p["D"] >= 32]
     if prec != "f32" or not rot:
         return None
@@ -346,20 +347,20 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
     p = rot[0]
     ms = per_instance[0]["kernels_ms"]
     N, D = p["N"], p["D"]
-    Np, Jp, Kp = -(-N // 128) * 128, -(-D // 128) * 128, -(-D // 64) * 64
+    Np, Jp, Kp = -(-N // 128) * 128, -(-D // 64) * 64, -(-D // 64) * 64
     t = ms["gemm_fit"] / 1e3
     peaks, which = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     achieved = 2.0 * N * D * D / t / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic_of("rot_gemm_fit", workload),
-            "traffic_algorithmic": 2 * 3 * (Np + Jp) * Kp,
-            "kernel": "rot_gemm_fit (tcgen05 split-BF16 GEMM + fitness epilogue)",
+            "traffic_algorithmic": 2 * 4 * (Np + Jp) * Kp,
+            "kernel": "rot_gemm_fit (tcgen05 exact integer-slice GEMM + fitness epilogue)",
             "kernel_ms_per_launch": ms["gemm_fit"],
-            "executed_tflops": 6 * 2.0 * Np * Jp * Kp / t / 1e12,
+            "executed_tflops": 10 * 2.0 * Np * Jp * Kp / t / 1e12,
             "peak_note": f"bf16 sustained {which} (kernel timed inside the generation sequence); "
-                         "achieved counts 2 N D^2 algorithmic flops, executed_tflops the six split "
-                         "BF16 products over padded extents",
+                         "achieved counts 2 N D^2 algorithmic flops, executed_tflops the ten "
+                         "BF16 slice products over padded extents",
             "kernels_ms": ms, "instance": {"fn": p["fn"], "N": N, "D": D},
             "per_instance": per_instance}
 

@@ -515,10 +515,10 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     r.D = D;
     r.N = N;
     r.Np = (int)((N + tc::BM - 1) / tc::BM * tc::BM);
-    r.Jp = (D + tc::BN - 1) / tc::BN * tc::BN;
+    r.Jp = (D + tc::SBN - 1) / tc::SBN * tc::SBN;
     r.Kp = (D + tc::BK - 1) / tc::BK * tc::BK;
-    r.nJt = r.Jp / tc::BN;
-    r.zc = tc::z_err_per_s(r.Kp);
+    r.nJt = r.Jp / tc::SBN;
+    if (r.Kp > tc::S_MAX_K) return fail(PSSO_ERR_UNSUPPORTED, "tensor pipeline: D above the slice GEMM's exact range");
     size_t off = 0;
     auto take = [&](size_t bytes) {
         off = align_up(off, 256);
@@ -526,8 +526,9 @@ psso_status setup_tc(psso_ctx* h, size_t k)
         off += bytes;
         return at;
     };
-    const size_t oA = take((size_t)3 * r.Np * r.Kp * 2), oB = take((size_t)3 * r.Jp * r.Kp * 2),
-                 omn = take((size_t)r.Jp * 4), odn = take((size_t)r.Np * 4), osame = take((size_t)N * 4),
+    const size_t oA = take((size_t)tc::SLICES * r.Np * r.Kp * 2), oB = take((size_t)tc::SLICES * r.Jp * r.Kp * 2),
+                 oms = take((size_t)r.Jp * 4), oml1 = take((size_t)r.Jp * 4), ods = take((size_t)r.Np * 4),
+                 odl1 = take((size_t)r.Np * 4), osame = take((size_t)N * 4),
                  opart = take((size_t)N * r.nJt * 16), ol1 = take((size_t)N * 4), ol2 = take((size_t)N * 4),
                  oz = take((size_t)2 * N * I.Dp * 8), oz0 = take((size_t)I.Dp * 8),
                  octl = take(sizeof(rot::RotCtl)), ol3 = take((size_t)N * 4),
@@ -539,8 +540,10 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     char* b = static_cast<char*>(R.mem);
     r.A = reinterpret_cast<__nv_bfloat16*>(b + oA);
     R.B = reinterpret_cast<__nv_bfloat16*>(b + oB);
-    r.mnorm = reinterpret_cast<float*>(b + omn);
-    r.dnorm = reinterpret_cast<float*>(b + odn);
+    r.mscale = reinterpret_cast<float*>(b + oms);
+    r.ml1 = reinterpret_cast<float*>(b + oml1);
+    r.dscale = reinterpret_cast<float*>(b + ods);
+    r.dl1 = reinterpret_cast<float*>(b + odl1);
     r.same = reinterpret_cast<uint32_t*>(b + osame);
     r.part = reinterpret_cast<float4*>(b + opart);
     r.list1 = reinterpret_cast<int32_t*>(b + ol1);
@@ -565,7 +568,8 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     R.z64_grid = 2 * prop.multiProcessorCount;
     R.z32_grid = 8 * prop.multiProcessorCount;
     R.fix_grid = prop.multiProcessorCount;
-    if (!tc::make_tmap_bf16(&R.tmA, r.A, r.Kp, 3 * r.Np) || !tc::make_tmap_bf16(&R.tmB, R.B, r.Kp, 3 * r.Jp))
+    if (!tc::make_tmap_bf16(&R.tmA, r.A, r.Kp, tc::SLICES * r.Np) ||
+        !tc::make_tmap_bf16(&R.tmB, R.B, r.Kp, tc::SLICES * r.Jp, tc::SBN))
         return fail(PSSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core operands");
     CUDA_TRY(rot::configure());
     CUDA_TRY(rot::build_constants(R, h->stream));

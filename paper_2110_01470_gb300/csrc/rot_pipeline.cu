@@ -84,12 +84,13 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
     const uint32_t gg = (uint32_t)g;
     const uint32_t ctr3r = TAG_RHO | (in.sid << 8), ctr3f = TAG_FRESH | (in.sid << 8);
     bool eqp = true;
-    float ss = 0.f;
-    const size_t plane = (size_t)r.Np * r.Kp;
-    __nv_bfloat16* arow = r.A + (size_t)i * r.Kp;
+    float dmax = 0.f, l1 = 0.f;
+    float dv[MAXC][4];
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
         const int c = lane + 32 * q;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) dv[q][m] = 0.f;
         if (c >= in.nchunks) continue;
         const int nvalid = min(4, in.D - 4 * c);
         const uint32_t valid = (1u << nvalid) - 1u;
@@ -117,32 +118,42 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
             }
         }
         st4(xr + 4 * c, x);
-        __nv_bfloat16 h[4], mm[4], l[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = 4 * c + m;
-            const float dv = (j < in.D) ? __fsub_rn(x[m], __ldg(in.o32 + j)) : 0.f;
-            ss = __fmaf_rn(dv, dv, ss);
-            tc::split3(dv, h[m], mm[m], l[m]);
+            dv[q][m] = (j < in.D) ? __fsub_rn(x[m], __ldg(in.o32 + j)) : 0.f;
+            dmax = fmaxf(dmax, fabsf(dv[q][m]));
+            l1 = __fadd_ru(l1, fabsf(dv[q][m]));
         }
-        // 4 consecutive bf16 (8 bytes) per plane
-        auto pack = [](const __nv_bfloat16 (&v)[4]) {
-            uint2 u;
-            u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
-            u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
-            return u;
-        };
-        *reinterpret_cast<uint2*>(arow + 4 * c) = pack(h);
-        *reinterpret_cast<uint2*>(arow + plane + 4 * c) = pack(mm);
-        *reinterpret_cast<uint2*>(arow + 2 * plane + 4 * c) = pack(l);
     }
-    for (int off = 16; off > 0; off >>= 1) ss = __fadd_rn(ss, __shfl_xor_sync(0xffffffffu, ss, off));
+    for (int off = 16; off > 0; off >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+        l1 = __fadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, off));
+    }
     eqp = __all_sync(0xffffffffu, eqp);
+    // the integer slices of d / s_d (tc_gemm.cuh), four planes
+    const float sd = tc::slice_scale(dmax), inv = 1.f / sd;   // powers of two: exact
+    const size_t plane = (size_t)r.Np * r.Kp;
+    __nv_bfloat16* arow = r.A + (size_t)i * r.Kp;
+#pragma unroll
+    for (int q = 0; q < MAXC; ++q) {
+        const int c = lane + 32 * q;
+        if (c >= in.nchunks) continue;
+        __nv_bfloat16 sl[4][tc::SLICES];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) tc::slice4(__fmul_rn(dv[q][m], inv), sl[m]);
+#pragma unroll
+        for (int p = 0; p < tc::SLICES; ++p) {
+            // 4 consecutive bf16 (8 bytes) per plane
+            uint2 u;
+            u.x = (uint32_t)__bfloat16_as_ushort(sl[0][p]) | ((uint32_t)__bfloat16_as_ushort(sl[1][p]) << 16);
+            u.y = (uint32_t)__bfloat16_as_ushort(sl[2][p]) | ((uint32_t)__bfloat16_as_ushort(sl[3][p]) << 16);
+            *reinterpret_cast<uint2*>(arow + p * plane + 4 * c) = u;
+        }
+    }
     if (lane == 0) {
-        // sum of 4 MAXC products per lane and 5 butterfly levels: relative error
-        // below (4 MAXC + 6) u; the bound is rounded up
-        const float rel = 1.02f * (float)(4 * MAXC + 6) * 0x1p-24f;
-        r.dnorm[i] = __fsqrt_ru(__fmul_ru(ss, 1.f + rel));
+        r.dscale[i] = sd;
+        r.dl1[i] = l1;
         r.same[i] = (g > 0 && eqp) ? 1u : 0u;
     }
 }
@@ -163,7 +174,9 @@ __global__ void rot_update(const RotDev r)
 }
 
 // ---- 2. GEMM with the fitness epilogue ------------------------------------------
-// Per element z~ with error ez <= zc ||d|| ||M_j|| + u |z~| (see tc_gemm.cuh),
+// Per element z~ with error ez (the integer-slice GEMM of tc_gemm.cuh: dropped
+// slice products and remainders, the FP32 join, and the roundings of d and M
+// to float, all against the FP64 rotation M (x - o)),
 // the terms and bounds of the rotated functions (as in the FP32 path of the
 // persistent kernel): ellipsoid w z^2; Rastrigin z^2 + 20 sin^2(pi z);
 // Ackley z^2 and sin^2(pi z) (two sums).  Sums: 32 terms per column block,
@@ -196,24 +209,31 @@ __device__ __forceinline__ void term32(int fn, float zt, float ez, const float* 
 struct FitEpi {
     const RotDev* r;
     int fn, D;
-    float dn, acc, acc2, accE, rQ;
-    __device__ void operator()(int c, const float (&z)[32])
+    float ds, dl1, drop;          // s_d, sum |d_k|, SLICE_DROP * D
+    float acc, acc2, accE, rQ;
+    __device__ void operator()(int c, const float (&tj)[32], const float (&em)[32])
     {
-        const int j0 = blockIdx.y * BN + 32 * c;
+        const int j0 = blockIdx.y * tc::SBN + 32 * c;
         float s = 0.f, s2 = 0.f, e = 0.f, eq = 0.f;
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
             const int j = j0 + t;
             if (j >= D) break;
-            const float zt = z[t];
-            const float ez = 1.01f * __fmaf_rn(r->zc * dn, __ldg(r->mnorm + j), 0x1p-24f * fabsf(zt));
+            const float sm = __ldg(r->mscale + j), l1m = __ldg(r->ml1 + j);
+            const float sc = __fmul_rn(ds, sm);                 // a power of two
+            const float zt = __fmul_rn(tj[t], __fmul_rn(sc, 0x1p-12f));
+            const float rd = __fmul_rn(sm, dl1), rm = __fmul_rn(ds, l1m);
+            // dropped slice products, slice remainders, d and M rounded to
+            // float (and the FP64 reference's own rounding), the FP32 join
+            const float ez = 1.01f * (drop * sc + tc::SLICE_REM * (rd + rm) + 2.03f * 0x1p-24f * fminf(rd, rm) +
+                                      0x1p-36f * em[t] * sc) + 0x1p-126f;
             term32(fn, zt, ez, r->inst_w32, j, s, s2, e, eq);
         }
         acc = __fadd_rn(acc, s);
         acc2 = __fadd_rn(acc2, s2);
         accE = __fadd_rn(accE, e);
         rQ = __fadd_rn(rQ, eq);
-        if (c == BN / 32 - 1) {
+        if (c == tc::SBN / 32 - 1) {
             const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
             if (i < r->N && PSSO_CHK(blockIdx.y < (unsigned)r->nJt, CHK_TILE, blockIdx.y))
                 r->part[i * r->nJt + blockIdx.y] = make_float4(acc, acc2, accE, rQ);
@@ -226,9 +246,10 @@ __global__ void __launch_bounds__(128, 1)
                  const __grid_constant__ RotDev r)
 {
     const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
-    FitEpi epi{&r, base_fn(r.fn), r.D, i < r.N ? r.dnorm[i] : 0.f, 0.f, 0.f, 0.f, 0.f};
+    FitEpi epi{&r,  base_fn(r.fn), r.D, i < r.N ? r.dscale[i] : 1.f, i < r.N ? r.dl1[i] : 0.f,
+               tc::SLICE_DROP * (float)r.D, 0.f, 0.f, 0.f, 0.f};
     tc::GemmArgs a{r.Np, r.Jp, r.Kp, &r.ctl->status};
-    tc::gemm_tile(&tmA, &tmB, a, epi);
+    tc::gemm_tile_sliced(&tmA, &tmB, a, epi);
 }
 
 // ---- 3. FP32 decisions ------------------------------------------------------------
@@ -746,7 +767,7 @@ cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent
     const int wpb = 8;
     rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();
-    rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / BN), 128, tc::SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
+    rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / tc::SBN), 128, tc::S_SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
     mark();
     rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();
@@ -811,6 +832,51 @@ cudaError_t run_generations(const RotHost& h, long long count, cudaStream_t s)
     return cudaSuccess;
 }
 
+// B planes of the integer-slice GEMM: one block per row j of the padded
+// [Jp][Kp] planes (rows >= D and columns >= D are zero), its scale s_M and
+// sum_k |M32_jk| (rounded up).
+__global__ void slice_matrix(const float* __restrict__ M32, int D, int Jp, int Kp, __nv_bfloat16* B,
+                             float* mscale, float* ml1)
+{
+    const int j = blockIdx.x;
+    float mx = 0.f, l1 = 0.f;
+    for (int k = threadIdx.x; k < D; k += blockDim.x) {
+        const float v = j < D ? M32[(size_t)j * D + k] : 0.f;
+        mx = fmaxf(mx, fabsf(v));
+        l1 = __fadd_ru(l1, fabsf(v));
+    }
+    __shared__ float rmx[32], rl1[32];
+    __shared__ float sm;
+    for (int off = 16; off > 0; off >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        l1 = __fadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rmx[threadIdx.x >> 5] = mx;
+        rl1[threadIdx.x >> 5] = l1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f, t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            m = fmaxf(m, rmx[w]);
+            t = __fadd_ru(t, rl1[w]);
+        }
+        sm = tc::slice_scale(m);
+        mscale[j] = sm;
+        ml1[j] = t;
+    }
+    __syncthreads();
+    const float inv = 1.f / sm;
+    const size_t plane = (size_t)Jp * Kp;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        const float v = (j < D && k < D) ? M32[(size_t)j * D + k] : 0.f;
+        __nv_bfloat16 sl[tc::SLICES];
+        tc::slice4(__fmul_rn(v, inv), sl);
+        for (int p = 0; p < tc::SLICES; ++p) B[p * plane + (size_t)j * Kp + k] = sl[p];
+    }
+}
+
 cudaError_t build_constants(const RotHost& h, cudaStream_t s)
 {
     const RotDev& r = h.dev;
@@ -818,7 +884,8 @@ cudaError_t build_constants(const RotHost& h, cudaStream_t s)
     split_m64<<<(unsigned)std::min<long long>((DD + 255) / 256, 4096), 256, 0, s>>>(h.M64, DD, h.Mh, h.Ml);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return tc::launch_split_matrix(h.M32, r.D, r.Jp, r.Kp, h.B, r.mnorm, s);
+    slice_matrix<<<r.Jp, 256, 0, s>>>(h.M32, r.D, r.Jp, r.Kp, h.B, r.mscale, r.ml1);
+    return cudaGetLastError();
 }
 
 cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s)
@@ -829,7 +896,7 @@ cudaError_t set_generation(const RotHost& h, long long g, cudaStream_t s)
 
 cudaError_t configure()
 {
-    return cudaFuncSetAttribute(rot_gemm_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    return cudaFuncSetAttribute(rot_gemm_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::S_SMEM_BYTES);
 }
 
 }  // namespace rot

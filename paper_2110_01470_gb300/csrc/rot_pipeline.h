@@ -31,11 +31,12 @@ struct RotDev {
     const float* inst_w32;
     int fn, D;
     long long N;
-    int Np, Jp, Kp, nJt;           // padded extents, 128-column tiles
-    float zc;                      // z error per unit of ||d|| ||M_j||
-    __nv_bfloat16* A;              // [3][Np][Kp] split planes of d = x - o
-    float* mnorm;                  // [Jp] bound on ||M32_j||
-    float* dnorm;                  // [Np] bound on ||d_i||
+    int Np, Jp, Kp, nJt;           // padded extents, tc::SBN-column tiles
+    __nv_bfloat16* A;              // [4][Np][Kp] integer slices of d = fl32(x - o) (tc_gemm.cuh)
+    float* dscale;                 // [Np] slice scale s_d of particle i (a power of two)
+    float* dl1;                    // [Np] sum_k |d_ik|, rounded up
+    float* mscale;                 // [Jp] slice scale s_M of output j
+    float* ml1;                    // [Jp] sum_k |M32_jk|, rounded up
     uint32_t* same;                // [N] x_i equals pBest_i bit for bit
     float4* part;                  // [N][nJt] tile sums (s1, s2, e1, e2)
     int32_t* list1;                // [N] pBest updates undecided by the GEMM bounds
@@ -53,7 +54,7 @@ struct RotDev {
 struct RotHost {
     RotDev dev;
     CUtensorMap tmA, tmB;
-    __nv_bfloat16* B;              // [3][Jp][Kp] split planes of M32
+    __nv_bfloat16* B;              // [4][Jp][Kp] integer slices of M32
     float* Mh;                     // float pair of M (refinement)
     float* Ml;
     const float* M32;

@@ -15,7 +15,7 @@
 namespace psso {
 namespace tc {
 
-bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows)
+bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows, int box_rows)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
@@ -30,7 +30,7 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows)
     if (!encode) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

@@ -350,8 +350,201 @@ __device__ __forceinline__ bool gemm_tile(const CUtensorMap* tmA, const CUtensor
     return good;
 }
 
-// Host: tensor map of a [rows][Kp] bf16 matrix, boxes of 64 x 128, 128-byte swizzle.
-bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows);
+// Host: tensor map of a [rows][Kp] bf16 matrix, boxes of 64 x box_rows,
+// 128-byte swizzle.
+bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows, int box_rows = BM);
+
+// ---------------------------------------------------------------------------
+// Exact integer-slice GEMM (the tensor pipeline's rotation).
+//
+// Each operand row is scaled by a power of two s (s_d per particle, s_M per
+// output j) such that every entry satisfies |v| <= 63/64 s, and written as
+// four 6-bit integer slices,
+//     v = s (V0 2^-6 + V1 2^-12 + V2 2^-18 + V3 2^-24 + r),  |r| <= 2^-25,
+// |V0| <= 63, |V1..V3| <= 32 (successive round-to-nearest; every step is
+// exact in FP32, slicer below).  The slice products of weight w = s + t <= 3
+// are accumulated, one accumulator per weight:
+//     acc_w = sum_k sum_{s+t=w} D_s,k M_t,jk,    w = 0 .. 3 (1, 2, 3, 4 MMAs)
+// Every product is an integer of magnitude <= 63 * 63, and for K <= 1024 every
+// partial sum of every accumulator stays below 1024 * 6080 < 2^23: an FP32
+// accumulator represents all of them exactly, so the accumulation is exact
+// whatever the MMA datapath's alignment and rounding (at least 24 bits).
+// The products of weight 4 .. 6 and the remainders r are dropped and bounded:
+// per k,
+//     s_d s_M (3.04 2^-26 + 3 2^-50) + 2^-25 (s_M |d_k| + s_d |M_jk|).
+// The epilogue joins the accumulators in FP32 from the smallest weight up,
+// t = acc_0 + 2^-6 acc_1 + 2^-12 acc_2 + 2^-18 acc_3 (three rounded
+// additions), and z = 2^-12 s_d s_M t exactly.
+constexpr int SBN = 64;                                     // output columns per tile
+constexpr int SLICES = 4;
+constexpr int S_A_BYTES = BM * BK * 2;                      // 16 KiB
+constexpr int S_B_BYTES = SBN * BK * 2;                     // 8 KiB
+constexpr int S_STAGE_BYTES = SLICES * (S_A_BYTES + S_B_BYTES);   // 96 KiB
+constexpr int S_SMEM_BYTES = STAGES * S_STAGE_BYTES + 1024;
+constexpr int S_TMEM_COLS = 256;                            // four accumulators of 64 columns
+constexpr int S_MAX_K = 1024;                               // exactness of the accumulators
+constexpr float SLICE_DROP = 3.04f * 0x1p-26f + 3.f * 0x1p-50f;   // per k, units of s_d s_M
+constexpr float SLICE_REM = 0x1p-25f;                             // per k, of s_M |d_k| + s_d |M_jk|
+
+// Power-of-two scale s of a row with max |v| = vmax: vmax <= 63/64 s (1 if vmax is 0).
+__host__ __device__ inline float slice_scale(float vmax)
+{
+    if (!(vmax > 0.f)) return 1.f;
+    int e = 0;
+    const float m = vmax * (64.f / 63.f) * (1.f + 0x1p-20f);   // rounded up
+    (void)frexpf(m, &e);                                          // m < 2^e
+    return ldexpf(1.f, e);
+}
+
+// The four slices of u = v / s (|u| <= 63/64) as BF16 integers.
+__device__ __forceinline__ void slice4(float u, __nv_bfloat16 (&o)[SLICES])
+{
+    float w = __fmul_rn(u, 64.f);
+#pragma unroll
+    for (int q = 0; q < SLICES; ++q) {
+        const float iq = rintf(w);
+        o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 63
+        w = __fmul_rn(__fsub_rn(w, iq), 64.f);       // both steps exact
+    }
+}
+
+// The GEMM main loop of tile (blockIdx.x, blockIdx.y) over SLICES A planes
+// [SLICES][Np][Kp] and B planes [SLICES][Jp][Kp] (Jp a multiple of SBN, Kp of
+// BK, Kp <= S_MAX_K).  The epilogue functor gets (column block c of 32,
+// t[32], em[32]) with t the joined accumulators and em = |t2| + |t1| + |t0|,
+// the magnitudes of the three rounded partial sums.  Returns false (all
+// threads) if a wait ran out.
+template <class Epi>
+__device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                                 const GemmArgs& a, Epi& epi)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * SBN;
+    const int nkb = a.Kp / BK;
+    const uint32_t sbase = smem_u32(smem);
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+    const uint32_t done = smem_u32(&bars[2 * STAGES]);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+        failed = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tmem_slot), S_TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer: per K block, the four A slices and the four B slices
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(empty(s), (uint32_t)((kb / STAGES - 1) & 1))) {
+                failed = 1;
+                break;
+            }
+            mbar_expect_tx(full(s), S_STAGE_BYTES);
+            const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
+            for (int p = 0; p < SLICES; ++p) {
+                tma_load_2d(st + (uint32_t)(p * S_A_BYTES), tmA, kb * BK, p * a.Np + m0, full(s));
+                tma_load_2d(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES), tmB, kb * BK, p * a.Jp + n0,
+                            full(s));
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: acc_w += sum_{s+t=w} A_s B_t^T
+        constexpr uint32_t idesc = idesc_bf16(BM, SBN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(full(s), (uint32_t)((kb / STAGES) & 1))) {
+                failed = 1;
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint32_t off = (uint32_t)(ks * 32);   // 16 bf16 along K
+                uint64_t ad[SLICES], bd[SLICES];
+#pragma unroll
+                for (int p = 0; p < SLICES; ++p) {
+                    ad[p] = sdesc_sw128(st + (uint32_t)(p * S_A_BYTES) + off);
+                    bd[p] = sdesc_sw128(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES) + off);
+                }
+                const uint32_t first = (kb | ks) ? 1u : 0u;
+#pragma unroll
+                for (int w = 0; w < SLICES; ++w) {
+                    const uint32_t acc = tmem + (uint32_t)(w * SBN);
+#pragma unroll
+                    for (int q = 0; q <= w; ++q) mma_bf16(acc, ad[q], bd[w - q], idesc, q ? 1u : first);
+                }
+            }
+            mma_commit(empty(s));      // the stage is free once these MMAs are done
+        }
+        mma_commit(done);              // all MMAs issued (possibly none if a wait failed)
+    }
+    __syncwarp();
+
+    bool ok = mbar_wait(done, 0u);
+    if (!ok) failed = 1;
+    tc_fence_after();
+    __syncthreads();
+    const bool good = !failed;
+    if (good) {
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+#pragma unroll 1
+        for (int c = 0; c < SBN / 32; ++c) {
+            float t[32], em[32], v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(3 * SBN + 32 * c), t);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) t[q] = __fmul_rn(t[q], 0x1p-18f);   // exact
+            tmem_ld32(tmem + lane_base + (uint32_t)(2 * SBN + 32 * c), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                t[q] = __fmaf_rn(v[q], 0x1p-12f, t[q]);   // one rounding (the product is exact)
+                em[q] = fabsf(t[q]);
+            }
+            tmem_ld32(tmem + lane_base + (uint32_t)(1 * SBN + 32 * c), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                t[q] = __fmaf_rn(v[q], 0x1p-6f, t[q]);
+                em[q] = __fadd_ru(em[q], fabsf(t[q]));
+            }
+            tmem_ld32(tmem + lane_base + (uint32_t)(32 * c), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                t[q] = __fadd_rn(v[q], t[q]);
+                em[q] = __fadd_ru(em[q], fabsf(t[q]));
+            }
+            epi(c, t, em);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, S_TMEM_COLS);
+    }
+    if (!good && threadIdx.x == 0 && a.status) atomicExch(a.status, 1);
+    return good;
+}
 
 }  // namespace tc
 }  // namespace psso
