@@ -85,12 +85,12 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
     const uint32_t ctr3r = TAG_RHO | (in.sid << 8), ctr3f = TAG_FRESH | (in.sid << 8);
     bool eqp = true;
     float dmax = 0.f, l1 = 0.f;
-    float dv[MAXC][4];
+    float dv[MAXC][4], dl[MAXC][4];    // d = x - o exactly, as a float pair
 #pragma unroll
     for (int q = 0; q < MAXC; ++q) {
         const int c = lane + 32 * q;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) dv[q][m] = 0.f;
+        for (int m = 0; m < 4; ++m) dv[q][m] = dl[q][m] = 0.f;
         if (c >= in.nchunks) continue;
         const int nvalid = min(4, in.D - 4 * c);
         const uint32_t valid = (1u << nvalid) - 1u;
@@ -121,7 +121,12 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = 4 * c + m;
-            dv[q][m] = (j < in.D) ? __fsub_rn(x[m], __ldg(in.o32 + j)) : 0.f;
+            if (j < in.D) {
+                const float a = x[m], b = -__ldg(in.o32 + j);
+                const float sum = __fadd_rn(a, b), bb = __fsub_rn(sum, a);   // TwoSum
+                dv[q][m] = sum;
+                dl[q][m] = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb));
+            }
             dmax = fmaxf(dmax, fabsf(dv[q][m]));
             l1 = __fadd_ru(l1, fabsf(dv[q][m]));
         }
@@ -131,6 +136,8 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
         l1 = __fadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, off));
     }
     eqp = __all_sync(0xffffffffu, eqp);
+    // |d| <= |fl(d)| (1 + 2^-24): the scale and the L1 norm cover the exact d
+    l1 = __fmul_ru(l1, 1.f + 0x1p-22f);
     // the integer slices of d / s_d (tc_gemm.cuh), four planes
     const float sd = tc::slice_scale(dmax), inv = 1.f / sd;   // powers of two: exact
     const size_t plane = (size_t)r.Np * r.Kp;
@@ -141,7 +148,7 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
         if (c >= in.nchunks) continue;
         __nv_bfloat16 sl[4][tc::SLICES];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) tc::slice4(__fmul_rn(dv[q][m], inv), sl[m]);
+        for (int m = 0; m < 4; ++m) tc::slice4_pair(__fmul_rn(dv[q][m], inv), __fmul_rn(dl[q][m], inv), sl[m]);
 #pragma unroll
         for (int p = 0; p < tc::SLICES; ++p) {
             // 4 consecutive bf16 (8 bytes) per plane
@@ -174,9 +181,9 @@ __global__ void rot_update(const RotDev r)
 }
 
 // ---- 2. GEMM with the fitness epilogue ------------------------------------------
-// Per element z~ with error ez (the integer-slice GEMM of tc_gemm.cuh: dropped
-// slice products and remainders, the FP32 join, and the roundings of d and M
-// to float, all against the FP64 rotation M (x - o)),
+// Per element z~ with error ez (the integer-slice GEMM of tc_gemm.cuh of the
+// exact d = x - o and the FP64 M: dropped slice products and remainders, the
+// FP32 join, against the FP64 rotation M (x - o)),
 // the terms and bounds of the rotated functions (as in the FP32 path of the
 // persistent kernel): ellipsoid w z^2; Rastrigin z^2 + 20 sin^2(pi z);
 // Ackley z^2 and sin^2(pi z) (two sums).  Sums: 32 terms per column block,
@@ -223,9 +230,9 @@ struct FitEpi {
             const float sc = __fmul_rn(ds, sm);                 // a power of two
             const float zt = __fmul_rn(tj[t], __fmul_rn(sc, 0x1p-12f));
             const float rd = __fmul_rn(sm, dl1), rm = __fmul_rn(ds, l1m);
-            // dropped slice products, slice remainders, d and M rounded to
-            // float (and the FP64 reference's own rounding), the FP32 join
-            const float ez = 1.01f * (drop * sc + tc::SLICE_REM * (rd + rm) + 2.03f * 0x1p-24f * fminf(rd, rm) +
+            // dropped slice products, slice remainders, the FP64 reference's
+            // own rounding (D <= 2^13 terms: 2^-40 sum |M||d|), the FP32 join
+            const float ez = 1.01f * (drop * sc + tc::SLICE_REM * (rd + rm) + 0x1p-40f * fminf(rd, rm) +
                                       0x1p-36f * em[t] * sc) + 0x1p-126f;
             term32(fn, zt, ez, r->inst_w32, j, s, s2, e, eq);
         }
@@ -832,24 +839,24 @@ cudaError_t run_generations(const RotHost& h, long long count, cudaStream_t s)
     return cudaSuccess;
 }
 
-// B planes of the integer-slice GEMM: one block per row j of the padded
-// [Jp][Kp] planes (rows >= D and columns >= D are zero), its scale s_M and
-// sum_k |M32_jk| (rounded up).
-__global__ void slice_matrix(const float* __restrict__ M32, int D, int Jp, int Kp, __nv_bfloat16* B,
+// B planes of the integer-slice GEMM from the FP64 rotation: one block per
+// row j of the padded [Jp][Kp] planes (rows >= D and columns >= D are zero),
+// its scale s_M and sum_k |M_jk| (rounded up).
+__global__ void slice_matrix(const double* __restrict__ M64, int D, int Jp, int Kp, __nv_bfloat16* B,
                              float* mscale, float* ml1)
 {
     const int j = blockIdx.x;
-    float mx = 0.f, l1 = 0.f;
+    double mx = 0.0, l1 = 0.0;
     for (int k = threadIdx.x; k < D; k += blockDim.x) {
-        const float v = j < D ? M32[(size_t)j * D + k] : 0.f;
-        mx = fmaxf(mx, fabsf(v));
-        l1 = __fadd_ru(l1, fabsf(v));
+        const double v = j < D ? M64[(size_t)j * D + k] : 0.0;
+        mx = fmax(mx, fabs(v));
+        l1 = __dadd_ru(l1, fabs(v));
     }
-    __shared__ float rmx[32], rl1[32];
+    __shared__ double rmx[32], rl1[32];
     __shared__ float sm;
     for (int off = 16; off > 0; off >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        l1 = __fadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, off));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        l1 = __dadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, off));
     }
     if ((threadIdx.x & 31) == 0) {
         rmx[threadIdx.x >> 5] = mx;
@@ -857,22 +864,22 @@ __global__ void slice_matrix(const float* __restrict__ M32, int D, int Jp, int K
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float m = 0.f, t = 0.f;
+        double m = 0.0, t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            m = fmaxf(m, rmx[w]);
-            t = __fadd_ru(t, rl1[w]);
+            m = fmax(m, rmx[w]);
+            t = __dadd_ru(t, rl1[w]);
         }
-        sm = tc::slice_scale(m);
+        sm = tc::slice_scale(__double2float_ru(m));
         mscale[j] = sm;
-        ml1[j] = t;
+        ml1[j] = __double2float_ru(t);
     }
     __syncthreads();
-    const float inv = 1.f / sm;
+    const double inv = 1.0 / (double)sm;
     const size_t plane = (size_t)Jp * Kp;
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
-        const float v = (j < D && k < D) ? M32[(size_t)j * D + k] : 0.f;
+        const double v = (j < D && k < D) ? M64[(size_t)j * D + k] : 0.0;
         __nv_bfloat16 sl[tc::SLICES];
-        tc::slice4(__fmul_rn(v, inv), sl);
+        tc::slice4_f64(__dmul_rn(v, inv), sl);
         for (int p = 0; p < tc::SLICES; ++p) B[p * plane + (size_t)j * Kp + k] = sl[p];
     }
 }
@@ -884,7 +891,7 @@ cudaError_t build_constants(const RotHost& h, cudaStream_t s)
     split_m64<<<(unsigned)std::min<long long>((DD + 255) / 256, 4096), 256, 0, s>>>(h.M64, DD, h.Mh, h.Ml);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    slice_matrix<<<r.Jp, 256, 0, s>>>(h.M32, r.D, r.Jp, r.Kp, h.B, r.mscale, r.ml1);
+    slice_matrix<<<r.Jp, 256, 0, s>>>(h.M64, r.D, r.Jp, r.Kp, h.B, r.mscale, r.ml1);
     return cudaGetLastError();
 }
 

@@ -358,35 +358,39 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows, int bo
 // Exact integer-slice GEMM (the tensor pipeline's rotation).
 //
 // Each operand row is scaled by a power of two s (s_d per particle, s_M per
-// output j) such that every entry satisfies |v| <= 63/64 s, and written as
-// four 6-bit integer slices,
-//     v = s (V0 2^-6 + V1 2^-12 + V2 2^-18 + V3 2^-24 + r),  |r| <= 2^-25,
-// |V0| <= 63, |V1..V3| <= 32 (successive round-to-nearest; every step is
-// exact in FP32, slicer below).  The slice products of weight w = s + t <= 3
-// are accumulated, one accumulator per weight:
-//     acc_w = sum_k sum_{s+t=w} D_s,k M_t,jk,    w = 0 .. 3 (1, 2, 3, 4 MMAs)
-// Every product is an integer of magnitude <= 63 * 63, and for K <= 1024 every
-// partial sum of every accumulator stays below 1024 * 6080 < 2^23: an FP32
-// accumulator represents all of them exactly, so the accumulation is exact
-// whatever the MMA datapath's alignment and rounding (at least 24 bits).
-// The products of weight 4 .. 6 and the remainders r are dropped and bounded:
-// per k,
-//     s_d s_M (3.04 2^-26 + 3 2^-50) + 2^-25 (s_M |d_k| + s_d |M_jk|).
+// output j) such that every entry satisfies |v| <= 63/64 s, and the exact
+// value (d = x - o as a float pair, M from its FP64 copy) is written as four
+// 6-bit integer slices,
+//     v = s (V0 2^-6 + V1 2^-12 + V2 2^-18 + V3 2^-24 + r),
+// |V0| <= 63, |V1..V3| <= 33, |r| <= 1.01 2^-25 (successive round-to-nearest
+// with exact steps, slicers below).  The slice products of weight
+// w = s + t <= 4 are accumulated, one accumulator per weight:
+//     acc_w = sum_k sum_{s+t=w} D_s,k M_t,jk,    w = 0 .. 4 (1, 2, 3, 4, 3 MMAs)
+// Every product is an integer; per k the weight-w products sum to at most
+// 3969, 4158, 5247, 6336, 3267, so for K <= 1024 every partial sum of every
+// accumulator stays below 2^23: an FP32 accumulator represents all of them
+// exactly, and the accumulation is exact whatever the MMA datapath's
+// alignment and rounding (24 bits suffice).  The products of weight 5 and 6
+// and the remainders r are dropped and bounded: per k,
+//     s_d s_M SLICE_DROP + SLICE_REM (s_M |d_k| + s_d |M_jk|).
 // The epilogue joins the accumulators in FP32 from the smallest weight up,
-// t = acc_0 + 2^-6 acc_1 + 2^-12 acc_2 + 2^-18 acc_3 (three rounded
-// additions), and z = 2^-12 s_d s_M t exactly.
+// t = acc_0 + 2^-6 acc_1 + 2^-12 acc_2 + 2^-18 acc_3 + 2^-24 acc_4 (four
+// rounded additions), and z = 2^-12 s_d s_M t exactly.
 constexpr int SBN = 64;                                     // output columns per tile
 constexpr int SLICES = 4;
+constexpr int SACC = 5;                                     // accumulators: weights 0 .. 4
 constexpr int S_A_BYTES = BM * BK * 2;                      // 16 KiB
 constexpr int S_B_BYTES = SBN * BK * 2;                     // 8 KiB
 constexpr int S_STAGE_BYTES = SLICES * (S_A_BYTES + S_B_BYTES);   // 96 KiB
 constexpr int S_SMEM_BYTES = STAGES * S_STAGE_BYTES + 1024;
-constexpr int S_TMEM_COLS = 256;                            // four accumulators of 64 columns
+constexpr int S_TMEM_COLS = 512;                            // five accumulators of 64 columns (allocation: a power of two)
 constexpr int S_MAX_K = 1024;                               // exactness of the accumulators
-constexpr float SLICE_DROP = 3.04f * 0x1p-26f + 3.f * 0x1p-50f;   // per k, units of s_d s_M
-constexpr float SLICE_REM = 0x1p-25f;                             // per k, of s_M |d_k| + s_d |M_jk|
+// weight 5 and 6: 2 * 33^2 * 2^-42 + 33^2 * 2^-48, and 3 r^2 (r <= 1.01 2^-25)
+constexpr float SLICE_DROP = 0.55f * 0x1p-30f;              // per k, units of s_d s_M
+constexpr float SLICE_REM = 1.01f * 0x1p-25f;               // per k, of s_M |d_k| + s_d |M_jk|
 
-// Power-of-two scale s of a row with max |v| = vmax: vmax <= 63/64 s (1 if vmax is 0).
+// Power-of-two scale s of a row with max |v| <= vmax (1 + 2^-22): every entry
+// satisfies |v| <= 63/64 s (s = 1 if vmax is 0).
 __host__ __device__ inline float slice_scale(float vmax)
 {
     if (!(vmax > 0.f)) return 1.f;
@@ -396,23 +400,43 @@ __host__ __device__ inline float slice_scale(float vmax)
     return ldexpf(1.f, e);
 }
 
-// The four slices of u = v / s (|u| <= 63/64) as BF16 integers.
-__device__ __forceinline__ void slice4(float u, __nv_bfloat16 (&o)[SLICES])
+// The four slices of u = u_hi + u_lo (an exact float pair, |u| <= 63/64) as
+// BF16 integers.  Each step keeps the rest exactly as a float pair: the
+// rounded-off part of the high word is exact, a TwoSum renormalises, and the
+// scaling by 64 is exact.  The rest after four slices is within 1.01 2^-25.
+__device__ __forceinline__ void slice4_pair(float u_hi, float u_lo, __nv_bfloat16 (&o)[SLICES])
 {
-    float w = __fmul_rn(u, 64.f);
+    float wh = __fmul_rn(u_hi, 64.f), wl = __fmul_rn(u_lo, 64.f);
 #pragma unroll
     for (int q = 0; q < SLICES; ++q) {
-        const float iq = rintf(w);
+        const float iq = rintf(wh);
         o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 63
-        w = __fmul_rn(__fsub_rn(w, iq), 64.f);       // both steps exact
+        const float r = __fsub_rn(wh, iq);           // exact
+        const float s = __fadd_rn(r, wl);            // TwoSum(r, wl)
+        const float bb = __fsub_rn(s, r);
+        const float e = __fadd_rn(__fsub_rn(r, __fsub_rn(s, bb)), __fsub_rn(wl, bb));
+        wh = __fmul_rn(s, 64.f);
+        wl = __fmul_rn(e, 64.f);
+    }
+}
+
+// The same for an FP64 value u (|u| <= 63/64): the steps are exact in FP64.
+__device__ __forceinline__ void slice4_f64(double u, __nv_bfloat16 (&o)[SLICES])
+{
+    double w = __dmul_rn(u, 64.0);
+#pragma unroll
+    for (int q = 0; q < SLICES; ++q) {
+        const double iq = rint(w);
+        o[q] = __float2bfloat16_rn((float)iq);
+        w = __dmul_rn(__dsub_rn(w, iq), 64.0);
     }
 }
 
 // The GEMM main loop of tile (blockIdx.x, blockIdx.y) over SLICES A planes
 // [SLICES][Np][Kp] and B planes [SLICES][Jp][Kp] (Jp a multiple of SBN, Kp of
 // BK, Kp <= S_MAX_K).  The epilogue functor gets (column block c of 32,
-// t[32], em[32]) with t the joined accumulators and em = |t2| + |t1| + |t0|,
-// the magnitudes of the three rounded partial sums.  Returns false (all
+// t[32], em[32]) with t the joined accumulators and em the sum of the
+// magnitudes of the four rounded partial sums.  Returns false (all
 // threads) if a wait ran out.
 template <class Epi>
 __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const CUtensorMap* tmB,
@@ -467,7 +491,7 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: acc_w += sum_{s+t=w} A_s B_t^T
+        // MMA issuer: acc_w += sum_{s+t=w} A_s B_t^T, w = 0 .. SACC-1
         constexpr uint32_t idesc = idesc_bf16(BM, SBN);
         bool ok = true;
         for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -490,10 +514,12 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
                 }
                 const uint32_t first = (kb | ks) ? 1u : 0u;
 #pragma unroll
-                for (int w = 0; w < SLICES; ++w) {
+                for (int w = 0; w < SACC; ++w) {
                     const uint32_t acc = tmem + (uint32_t)(w * SBN);
+                    const int q0 = w < SLICES ? 0 : w - (SLICES - 1);
+                    const int q1 = w < SLICES ? w : SLICES - 1;
 #pragma unroll
-                    for (int q = 0; q <= w; ++q) mma_bf16(acc, ad[q], bd[w - q], idesc, q ? 1u : first);
+                    for (int q = q0; q <= q1; ++q) mma_bf16(acc, ad[q], bd[w - q], idesc, q > q0 ? 1u : first);
                 }
             }
             mma_commit(empty(s));      // the stage is free once these MMAs are done
@@ -512,14 +538,20 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
 #pragma unroll 1
         for (int c = 0; c < SBN / 32; ++c) {
             float t[32], em[32], v[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(3 * SBN + 32 * c), t);
+            tmem_ld32(tmem + lane_base + (uint32_t)(4 * SBN + 32 * c), t);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) t[q] = __fmul_rn(t[q], 0x1p-18f);   // exact
+            for (int q = 0; q < 32; ++q) t[q] = __fmul_rn(t[q], 0x1p-24f);   // exact
+            tmem_ld32(tmem + lane_base + (uint32_t)(3 * SBN + 32 * c), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                t[q] = __fmaf_rn(v[q], 0x1p-18f, t[q]);   // one rounding (the product is exact)
+                em[q] = fabsf(t[q]);
+            }
             tmem_ld32(tmem + lane_base + (uint32_t)(2 * SBN + 32 * c), v);
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                t[q] = __fmaf_rn(v[q], 0x1p-12f, t[q]);   // one rounding (the product is exact)
-                em[q] = fabsf(t[q]);
+                t[q] = __fmaf_rn(v[q], 0x1p-12f, t[q]);
+                em[q] = __fadd_ru(em[q], fabsf(t[q]));
             }
             tmem_ld32(tmem + lane_base + (uint32_t)(1 * SBN + 32 * c), v);
 #pragma unroll

@@ -1,12 +1,16 @@
 """The arithmetic of the tensor pipeline's exact integer-slice GEMM, restated
-in numpy float32 on the CPU: the slice scale, the four 6-bit slices and the
-facts the bound rests on -- |V0| <= 63, |V1..V3| <= 32, the remainder below
-2^-25, every accumulator's partial sums below 2^23 for K <= 1024, and the
-dropped slice products within SLICE_DROP per k."""
+in numpy on the CPU: the slice scale, the four 6-bit slices of an exact float
+pair (d = x - o) and of an FP64 value (M), and the facts the bound rests on --
+|V0| <= 63, |V1..V3| <= 33, the rest within 1.01 2^-25, the weight-w products
+(w = 0..4) summing per k to at most 3969 / 4158 / 5247 / 6336 / 3267 so that
+K = 1024 partial sums stay below 2^23, and the dropped products of weight 5
+and 6 with the remainders within the per-k bound of the epilogue."""
 import numpy as np
 
 F = np.float32
-SLICE_DROP = 3.04 * 2.0 ** -26 + 3 * 2.0 ** -50
+SLICE_DROP = 0.55 * 2.0 ** -30
+SLICE_REM = 1.01 * 2.0 ** -25
+PER_K_MAX = (3969, 4158, 5247, 6336, 3267)
 
 
 def slice_scale(vmax):
@@ -17,69 +21,97 @@ def slice_scale(vmax):
     return F(np.ldexp(1.0, int(e)))
 
 
-def slice4(u):
-    """Slices of float32 u (|u| <= 63/64), each step in float32."""
-    w = F(u) * F(64.0)
+def two_sum(a, b):
+    s = F(a + b)
+    bb = F(s - a)
+    return s, F(F(a - F(s - bb)) + F(b - bb))
+
+
+def slice_pair(hi, lo):
+    """Slices of the float32 pair hi + lo, every step in float32."""
+    wh, wl = F(hi * F(64)), F(lo * F(64))
     out = []
     for _ in range(4):
-        q = np.rint(w).astype(F)
+        q = F(np.rint(wh))
+        out.append(float(q))
+        r = F(wh - q)
+        s, e = two_sum(r, wl)
+        wh, wl = F(s * F(64)), F(e * F(64))
+    return np.array(out)
+
+
+def slice_f64(u):
+    w = u * 64.0
+    out = []
+    for _ in range(4):
+        q = np.rint(w)
         out.append(q)
-        w = F(F(w - q) * F(64.0))
-    return np.array(out, dtype=np.float64)
+        w = (w - q) * 64.0
+    return np.array(out)
 
 
-def _rows(rng, n, D):
-    scale = 10.0 ** rng.uniform(-6, 3, (n, 1))
-    v = (rng.standard_normal((n, D)) * scale).astype(F)
-    v[0, :] = 0
-    v[1, :D // 2] = F(2.0 ** -140)          # subnormal-range values next to normal ones
-    return v
+def _d_rows(rng, n, D):
+    """d = x - o for float32 x and o, as exact float pairs (and in float64)."""
+    rows = []
+    for t in range(n):
+        scale = 10.0 ** rng.uniform(-3, 3)
+        x = (rng.uniform(-1, 1, D) * scale).astype(F)
+        o = (rng.uniform(-1, 1, D) * scale * rng.uniform(0, 2)).astype(F)
+        if t == 0:
+            x = o.copy()                                 # d = 0
+        pairs = [two_sum(a, F(-b)) for a, b in zip(x, o)]
+        hi = np.array([p[0] for p in pairs], F)
+        lo = np.array([p[1] for p in pairs], F)
+        exact = x.astype(np.float64) - o.astype(np.float64)
+        assert np.array_equal(hi.astype(np.float64) + lo.astype(np.float64), exact)
+        rows.append((hi, lo, exact))
+    return rows
+
+
+def _d_slices(hi, lo):
+    l1 = float(F(np.abs(hi).sum(dtype=np.float64) * (1 + 2.0 ** -22)))
+    sd = slice_scale(float(np.abs(hi).max()))
+    inv = F(1.0 / sd)
+    S = np.array([slice_pair(F(h * inv), F(l * inv)) for h, l in zip(hi, lo)])
+    return float(sd), S, l1
+
+
+def _m_slices(m):
+    sm = slice_scale(float(F(np.abs(m).max()) * F(1 + 2.0 ** -23)))
+    return float(sm), np.array([slice_f64(v / float(sm)) for v in m])
 
 
 def test_slices_reconstruct_within_remainder_bound():
     rng = np.random.default_rng(7)
-    for row in _rows(rng, 60, 257):
-        s = slice_scale(float(np.abs(row).max()))
-        assert np.abs(row).max() <= 63 / 64 * s
-        for v in row:
-            u = F(v) * F(1.0 / s)
-            sl = slice4(u)
-            assert abs(sl[0]) <= 63 and np.all(np.abs(sl[1:]) <= 32)
-            assert np.all(sl == np.rint(sl))
-            rec = sum(sl[q] * 64.0 ** -(q + 1) for q in range(4))
-            assert abs(float(u) - rec) <= 2.0 ** -25
-
-
-def test_edge_values():
-    for u in (63 / 64, -63 / 64, 0.5, 2.0 ** -24, 2.0 ** -25, 2.0 ** -26, 1 / 128 - 2.0 ** -30):
-        sl = slice4(F(u))
-        rec = sum(sl[q] * 64.0 ** -(q + 1) for q in range(4))
-        assert abs(float(F(u)) - rec) <= 2.0 ** -25
-        assert abs(sl[0]) <= 63 and np.all(np.abs(sl[1:]) <= 32)
+    for hi, lo, exact in _d_rows(rng, 20, 129):
+        sd, S, _ = _d_slices(hi, lo)
+        assert np.abs(exact).max() <= 63 / 64 * sd
+        assert np.all(np.abs(S[:, 0]) <= 63) and np.all(np.abs(S[:, 1:]) <= 33)
+        rec = S @ (64.0 ** -np.arange(1, 5))
+        assert np.all(np.abs(exact / sd - rec) <= SLICE_REM)
+    for _ in range(20):
+        m = rng.standard_normal(129) * 10.0 ** rng.uniform(-4, 1)
+        sm, S = _m_slices(m)
+        assert np.abs(m).max() <= 63 / 64 * sm
+        assert np.all(np.abs(S[:, 0]) <= 63) and np.all(np.abs(S[:, 1:]) <= 33)
+        assert np.all(np.abs(m / sm - S @ (64.0 ** -np.arange(1, 5))) <= SLICE_REM)
 
 
 def test_accumulators_exact_and_dropped_terms_bounded():
-    """Per k the weight-w slice products sum to at most 3969 / 4032 / 5056 /
-    6080, so K = 1024 partial sums stay below 2^23; the products of weight
-    4..6 and the remainders are within the per-k bound the epilogue uses."""
     rng = np.random.default_rng(11)
     D = 1000
-    d = _rows(rng, 6, D)
-    M = _rows(rng, 6, D)
-    for dr in d:
-        sd = slice_scale(float(np.abs(dr).max()))
-        Sd = np.array([slice4(F(v) * F(1.0 / sd)) for v in dr])          # [D][4]
-        for mr in M:
-            sm = slice_scale(float(np.abs(mr).max()))
-            Sm = np.array([slice4(F(v) * F(1.0 / sm)) for v in mr])
+    for hi, lo, exact in _d_rows(rng, 4, D):
+        sd, Sd, l1d = _d_slices(hi, lo)
+        assert np.abs(exact).sum() <= l1d
+        for _ in range(4):
+            m = rng.standard_normal(D) * 10.0 ** rng.uniform(-3, 0)
+            sm, Sm = _m_slices(m)
             kept = np.zeros(D)
-            for w in range(4):
-                prod = sum(Sd[:, q] * Sm[:, w - q] for q in range(w + 1))
-                assert np.abs(prod).max() <= (3969, 4032, 5056, 6080)[w]
+            for w in range(5):
+                prod = sum(Sd[:, q] * Sm[:, w - q] for q in range(max(0, w - 3), min(w, 3) + 1))
+                assert np.abs(prod).max() <= PER_K_MAX[w]
                 assert np.abs(prod).sum() < 2 ** 23
                 kept += prod * 64.0 ** -(w + 2)
-            exact = dr.astype(np.float64) * mr.astype(np.float64)
-            dropped = np.abs(exact - kept * float(sd) * float(sm))
-            bound = SLICE_DROP * float(sd) * float(sm) + 2.0 ** -25 * (
-                float(sm) * np.abs(dr.astype(np.float64)) + float(sd) * np.abs(mr.astype(np.float64)))
-            assert np.all(dropped <= bound * (1 + 1e-12))
+            dropped = np.abs(exact * m - kept * sd * sm)
+            bound = SLICE_DROP * sd * sm + SLICE_REM * (sm * np.abs(exact) + sd * np.abs(m))
+            assert np.all(dropped <= bound * (1 + 1e-9))
