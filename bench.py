@@ -331,8 +331,9 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
     """Rotated swarms on the tensor-core pipeline: per-kernel event timing of
     the first such instance (psso_time_kernels) and the roofline of the GEMM
     kernel.  Algorithmic work is z = M (x - o): 2 N D^2 flops per generation;
-    the kernel executes thirteen BF16 slice products (four 6-bit integer
-    slices per operand, weights 0..4) over the padded extents."""
+    the kernel executes ten BF16 slice products (four 7-bit integer slices per
+    operand, weights 0..3, in six exact accumulators) over the padded
+    extents."""
     rot = [p for p in problems if p["fn"].startswith("rot_") and p["N"] >= 128 and p["D"] >= 32]
     if prec != "f32" or not rot:
         return None
@@ -357,9 +358,9 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
             "traffic_algorithmic": 2 * 4 * (Np + Jp) * Kp,
             "kernel": "rot_gemm_fit (tcgen05 exact integer-slice GEMM + fitness epilogue)",
             "kernel_ms_per_launch": ms["gemm_fit"],
-            "executed_tflops": 13 * 2.0 * Np * Jp * Kp / t / 1e12,
+            "executed_tflops": 10 * 2.0 * Np * Jp * Kp / t / 1e12,
             "peak_note": f"bf16 sustained {which} (kernel timed inside the generation sequence); "
-                         "achieved counts 2 N D^2 algorithmic flops, executed_tflops the thirteen "
+                         "achieved counts 2 N D^2 algorithmic flops, executed_tflops the ten "
                          "BF16 slice products over padded extents",
             "kernels_ms": ms, "instance": {"fn": p["fn"], "N": N, "D": D},
             "per_instance": per_instance}

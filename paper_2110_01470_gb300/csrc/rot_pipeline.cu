@@ -138,7 +138,7 @@ __device__ void update_row(const RotDev& r, const Hot& in, int64_t i, int64_t g)
     eqp = __all_sync(0xffffffffu, eqp);
     // |d| <= |fl(d)| (1 + 2^-24): the scale and the L1 norm cover the exact d
     l1 = __fmul_ru(l1, 1.f + 0x1p-22f);
-    // the integer slices of d / s_d (tc_gemm.cuh), four planes
+    // the 7-bit integer slices of d / s_d (tc_gemm.cuh), four planes
     const float sd = tc::slice_scale(dmax), inv = 1.f / sd;   // powers of two: exact
     const size_t plane = (size_t)r.Np * r.Kp;
     __nv_bfloat16* arow = r.A + (size_t)i * r.Kp;
@@ -228,12 +228,12 @@ struct FitEpi {
             if (j >= D) break;
             const float sm = __ldg(r->mscale + j), l1m = __ldg(r->ml1 + j);
             const float sc = __fmul_rn(ds, sm);                 // a power of two
-            const float zt = __fmul_rn(tj[t], __fmul_rn(sc, 0x1p-12f));
+            const float zt = __fmul_rn(tj[t], __fmul_rn(sc, 0x1p-14f));
             const float rd = __fmul_rn(sm, dl1), rm = __fmul_rn(ds, l1m);
             // dropped slice products, slice remainders, the FP64 reference's
             // own rounding (D <= 2^13 terms: 2^-40 sum |M||d|), the FP32 join
             const float ez = 1.01f * (drop * sc + tc::SLICE_REM * (rd + rm) + 0x1p-40f * fminf(rd, rm) +
-                                      0x1p-36f * em[t] * sc) + 0x1p-126f;
+                                      0x1p-38f * em[t] * sc) + 0x1p-126f;
             term32(fn, zt, ez, r->inst_w32, j, s, s2, e, eq);
         }
         acc = __fadd_rn(acc, s);

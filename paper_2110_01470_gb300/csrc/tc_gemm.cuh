@@ -358,77 +358,80 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows, int bo
 // Exact integer-slice GEMM (the tensor pipeline's rotation).
 //
 // Each operand row is scaled by a power of two s (s_d per particle, s_M per
-// output j) such that every entry satisfies |v| <= 63/64 s, and the exact
+// output j) such that every entry satisfies |v| <= 127/128 s, and the exact
 // value (d = x - o as a float pair, M from its FP64 copy) is written as four
-// 6-bit integer slices,
-//     v = s (V0 2^-6 + V1 2^-12 + V2 2^-18 + V3 2^-24 + r),
-// |V0| <= 63, |V1..V3| <= 33, |r| <= 1.01 2^-25 (successive round-to-nearest
+// 7-bit integer slices,
+//     v = s (V0 2^-7 + V1 2^-14 + V2 2^-21 + V3 2^-28 + r),
+// |V0| <= 127, |V1..V3| <= 64, |r| <= 1.01 2^-29 (successive round-to-nearest
 // with exact steps, slicers below).  The slice products of weight
-// w = s + t <= 4 are accumulated, one accumulator per weight:
-//     acc_w = sum_k sum_{s+t=w} D_s,k M_t,jk,    w = 0 .. 4 (1, 2, 3, 4, 3 MMAs)
-// Every product is an integer; per k the weight-w products sum to at most
-// 3969, 4158, 5247, 6336, 3267, so for K <= 1024 every partial sum of every
-// accumulator stays below 2^23: an FP32 accumulator represents all of them
-// exactly, and the accumulation is exact whatever the MMA datapath's
-// alignment and rounding (24 bits suffice).  The products of weight 5 and 6
+// w = s + t <= 3 are accumulated in six accumulators, products of equal
+// weight sharing one as far as exactness allows:
+//     acc0: D0 M0        acc1: D0 M1 + D1 M0     acc2: D0 M2 + D2 M0
+//     acc3: D1 M1        acc4: D0 M3 + D3 M0     acc5: D1 M2 + D2 M1
+// (ten MMAs per K step).  Every product is an integer; per k an accumulator
+// gains at most 16256 (acc0 16129, acc3 4096, acc5 8192), so for K <= 1024
+// every partial sum stays below 2^24: an FP32 accumulator represents all of
+// them exactly, and the accumulation is exact whatever the MMA datapath's
+// alignment and rounding (24 bits suffice).  The products of weight 4 .. 6
 // and the remainders r are dropped and bounded: per k,
 //     s_d s_M SLICE_DROP + SLICE_REM (s_M |d_k| + s_d |M_jk|).
 // The epilogue joins the accumulators in FP32 from the smallest weight up,
-// t = acc_0 + 2^-6 acc_1 + 2^-12 acc_2 + 2^-18 acc_3 + 2^-24 acc_4 (four
-// rounded additions), and z = 2^-12 s_d s_M t exactly.
+// t = acc0 + 2^-7 acc1 + 2^-14 (acc2 + acc3) + 2^-21 (acc4 + acc5) (five
+// rounded operations), and z = 2^-14 s_d s_M t exactly.
 constexpr int SBN = 64;                                     // output columns per tile
 constexpr int SLICES = 4;
-constexpr int SACC = 5;                                     // accumulators: weights 0 .. 4
+constexpr int SACC = 6;                                     // accumulators
+constexpr int SPAIRS = 10;                                  // MMAs per K step
 constexpr int S_A_BYTES = BM * BK * 2;                      // 16 KiB
 constexpr int S_B_BYTES = SBN * BK * 2;                     // 8 KiB
 constexpr int S_STAGE_BYTES = SLICES * (S_A_BYTES + S_B_BYTES);   // 96 KiB
 constexpr int S_SMEM_BYTES = STAGES * S_STAGE_BYTES + 1024;
-constexpr int S_TMEM_COLS = 512;                            // five accumulators of 64 columns (allocation: a power of two)
+constexpr int S_TMEM_COLS = 512;                            // six accumulators of 64 columns (a power of two)
 constexpr int S_MAX_K = 1024;                               // exactness of the accumulators
-// weight 5 and 6: 2 * 33^2 * 2^-42 + 33^2 * 2^-48, and 3 r^2 (r <= 1.01 2^-25)
-constexpr float SLICE_DROP = 0.55f * 0x1p-30f;              // per k, units of s_d s_M
-constexpr float SLICE_REM = 1.01f * 0x1p-25f;               // per k, of s_M |d_k| + s_d |M_jk|
+// weight 4..6: 3 * 64^2 * 2^-42 + 2 * 64^2 * 2^-49 + 64^2 * 2^-56, and 3 r^2
+constexpr float SLICE_DROP = 3.04f * 0x1p-30f;              // per k, units of s_d s_M
+constexpr float SLICE_REM = 1.01f * 0x1p-29f;               // per k, of s_M |d_k| + s_d |M_jk|
 
 // Power-of-two scale s of a row with max |v| <= vmax (1 + 2^-22): every entry
-// satisfies |v| <= 63/64 s (s = 1 if vmax is 0).
+// satisfies |v| <= 127/128 s (s = 1 if vmax is 0).
 __host__ __device__ inline float slice_scale(float vmax)
 {
     if (!(vmax > 0.f)) return 1.f;
     int e = 0;
-    const float m = vmax * (64.f / 63.f) * (1.f + 0x1p-20f);   // rounded up
-    (void)frexpf(m, &e);                                          // m < 2^e
+    const float m = vmax * (128.f / 127.f) * (1.f + 0x1p-20f);   // rounded up
+    (void)frexpf(m, &e);                                            // m < 2^e
     return ldexpf(1.f, e);
 }
 
-// The four slices of u = u_hi + u_lo (an exact float pair, |u| <= 63/64) as
-// BF16 integers.  Each step keeps the rest exactly as a float pair: the
+// The four slices of u = u_hi + u_lo (an exact float pair, |u| <= 127/128)
+// as BF16 integers.  Each step keeps the rest exactly as a float pair: the
 // rounded-off part of the high word is exact, a TwoSum renormalises, and the
-// scaling by 64 is exact.  The rest after four slices is within 1.01 2^-25.
+// scaling by 128 is exact.  The rest after four slices is within 1.01 2^-29.
 __device__ __forceinline__ void slice4_pair(float u_hi, float u_lo, __nv_bfloat16 (&o)[SLICES])
 {
-    float wh = __fmul_rn(u_hi, 64.f), wl = __fmul_rn(u_lo, 64.f);
+    float wh = __fmul_rn(u_hi, 128.f), wl = __fmul_rn(u_lo, 128.f);
 #pragma unroll
     for (int q = 0; q < SLICES; ++q) {
         const float iq = rintf(wh);
-        o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 63
+        o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 127
         const float r = __fsub_rn(wh, iq);           // exact
         const float s = __fadd_rn(r, wl);            // TwoSum(r, wl)
         const float bb = __fsub_rn(s, r);
         const float e = __fadd_rn(__fsub_rn(r, __fsub_rn(s, bb)), __fsub_rn(wl, bb));
-        wh = __fmul_rn(s, 64.f);
-        wl = __fmul_rn(e, 64.f);
+        wh = __fmul_rn(s, 128.f);
+        wl = __fmul_rn(e, 128.f);
     }
 }
 
-// The same for an FP64 value u (|u| <= 63/64): the steps are exact in FP64.
+// The same for an FP64 value u (|u| <= 127/128): the steps are exact in FP64.
 __device__ __forceinline__ void slice4_f64(double u, __nv_bfloat16 (&o)[SLICES])
 {
-    double w = __dmul_rn(u, 64.0);
+    double w = __dmul_rn(u, 128.0);
 #pragma unroll
     for (int q = 0; q < SLICES; ++q) {
         const double iq = rint(w);
         o[q] = __float2bfloat16_rn((float)iq);
-        w = __dmul_rn(__dsub_rn(w, iq), 64.0);
+        w = __dmul_rn(__dsub_rn(w, iq), 128.0);
     }
 }
 
@@ -491,7 +494,7 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: acc_w += sum_{s+t=w} A_s B_t^T, w = 0 .. SACC-1
+        // MMA issuer: the ten slice products into the six accumulators
         constexpr uint32_t idesc = idesc_bf16(BM, SBN);
         bool ok = true;
         for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -513,14 +516,15 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
                     bd[p] = sdesc_sw128(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES) + off);
                 }
                 const uint32_t first = (kb | ks) ? 1u : 0u;
+                // (accumulator, A slice, B slice); the first product of each
+                // accumulator starts it at the first K step
+                constexpr int PA[SPAIRS] = {0, 0, 1, 0, 2, 1, 0, 3, 1, 2};
+                constexpr int PB[SPAIRS] = {0, 1, 0, 2, 0, 1, 3, 0, 2, 1};
+                constexpr int PACC[SPAIRS] = {0, 1, 1, 2, 2, 3, 4, 4, 5, 5};
+                constexpr int PLEAD[SPAIRS] = {1, 1, 0, 1, 0, 1, 1, 0, 1, 0};
 #pragma unroll
-                for (int w = 0; w < SACC; ++w) {
-                    const uint32_t acc = tmem + (uint32_t)(w * SBN);
-                    const int q0 = w < SLICES ? 0 : w - (SLICES - 1);
-                    const int q1 = w < SLICES ? w : SLICES - 1;
-#pragma unroll
-                    for (int q = q0; q <= q1; ++q) mma_bf16(acc, ad[q], bd[w - q], idesc, q > q0 ? 1u : first);
-                }
+                for (int q = 0; q < SPAIRS; ++q)
+                    mma_bf16(tmem + (uint32_t)(PACC[q] * SBN), ad[PA[q]], bd[PB[q]], idesc, PLEAD[q] ? first : 1u);
             }
             mma_commit(empty(s));      // the stage is free once these MMAs are done
         }
@@ -540,24 +544,22 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
             float t[32], em[32], v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)(4 * SBN + 32 * c), t);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) t[q] = __fmul_rn(t[q], 0x1p-24f);   // exact
-            tmem_ld32(tmem + lane_base + (uint32_t)(3 * SBN + 32 * c), v);
-#pragma unroll
             for (int q = 0; q < 32; ++q) {
-                t[q] = __fmaf_rn(v[q], 0x1p-18f, t[q]);   // one rounding (the product is exact)
-                em[q] = fabsf(t[q]);
+                t[q] = __fmul_rn(t[q], 0x1p-21f);   // exact
+                em[q] = 0.f;
             }
-            tmem_ld32(tmem + lane_base + (uint32_t)(2 * SBN + 32 * c), v);
+            // (accumulator, weight) from the smallest weight up; each step one
+            // rounding (the scaled accumulator is exact)
+            constexpr int JA[4] = {5, 3, 2, 1};
+            constexpr float JW[4] = {0x1p-21f, 0x1p-14f, 0x1p-14f, 0x1p-7f};
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                t[q] = __fmaf_rn(v[q], 0x1p-12f, t[q]);
-                em[q] = __fadd_ru(em[q], fabsf(t[q]));
-            }
-            tmem_ld32(tmem + lane_base + (uint32_t)(1 * SBN + 32 * c), v);
+            for (int st = 0; st < 4; ++st) {
+                tmem_ld32(tmem + lane_base + (uint32_t)(JA[st] * SBN + 32 * c), v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                t[q] = __fmaf_rn(v[q], 0x1p-6f, t[q]);
-                em[q] = __fadd_ru(em[q], fabsf(t[q]));
+                for (int q = 0; q < 32; ++q) {
+                    t[q] = __fmaf_rn(v[q], JW[st], t[q]);
+                    em[q] = __fadd_ru(em[q], fabsf(t[q]));
+                }
             }
             tmem_ld32(tmem + lane_base + (uint32_t)(32 * c), v);
 #pragma unroll

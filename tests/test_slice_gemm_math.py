@@ -1,22 +1,25 @@
 """The arithmetic of the tensor pipeline's exact integer-slice GEMM, restated
-in numpy on the CPU: the slice scale, the four 6-bit slices of an exact float
+in numpy on the CPU: the slice scale, the four 7-bit slices of an exact float
 pair (d = x - o) and of an FP64 value (M), and the facts the bound rests on --
-|V0| <= 63, |V1..V3| <= 33, the rest within 1.01 2^-25, the weight-w products
-(w = 0..4) summing per k to at most 3969 / 4158 / 5247 / 6336 / 3267 so that
-K = 1024 partial sums stay below 2^23, and the dropped products of weight 5
-and 6 with the remainders within the per-k bound of the epilogue."""
+|V0| <= 127, |V1..V3| <= 64, the rest within 1.01 2^-29, the six
+accumulators' products summing per k to at most 16129 / 16256 / 16256 / 4096 /
+16256 / 8192 so that K = 1024 partial sums stay below 2^24, and the dropped
+products of weight 4..6 with the remainders within the per-k bound of the
+epilogue."""
 import numpy as np
 
 F = np.float32
-SLICE_DROP = 0.55 * 2.0 ** -30
-SLICE_REM = 1.01 * 2.0 ** -25
-PER_K_MAX = (3969, 4158, 5247, 6336, 3267)
+SLICE_DROP = 3.04 * 2.0 ** -30
+SLICE_REM = 1.01 * 2.0 ** -29
+# (A slice, B slice) pairs of each accumulator, its weight, its per-k maximum
+ACCS = [([(0, 0)], 0, 16129), ([(0, 1), (1, 0)], 1, 16256), ([(0, 2), (2, 0)], 2, 16256),
+        ([(1, 1)], 2, 4096), ([(0, 3), (3, 0)], 3, 16256), ([(1, 2), (2, 1)], 3, 8192)]
 
 
 def slice_scale(vmax):
     if not vmax > 0:
         return F(1.0)
-    m = F(F(F(vmax) * F(64.0 / 63.0)) * F(1 + 2.0 ** -20))
+    m = F(F(F(vmax) * F(128.0 / 127.0)) * F(1 + 2.0 ** -20))
     _, e = np.frexp(m)
     return F(np.ldexp(1.0, int(e)))
 
@@ -29,24 +32,24 @@ def two_sum(a, b):
 
 def slice_pair(hi, lo):
     """Slices of the float32 pair hi + lo, every step in float32."""
-    wh, wl = F(hi * F(64)), F(lo * F(64))
+    wh, wl = F(hi * F(128)), F(lo * F(128))
     out = []
     for _ in range(4):
         q = F(np.rint(wh))
         out.append(float(q))
         r = F(wh - q)
         s, e = two_sum(r, wl)
-        wh, wl = F(s * F(64)), F(e * F(64))
+        wh, wl = F(s * F(128)), F(e * F(128))
     return np.array(out)
 
 
 def slice_f64(u):
-    w = u * 64.0
+    w = u * 128.0
     out = []
     for _ in range(4):
         q = np.rint(w)
         out.append(q)
-        w = (w - q) * 64.0
+        w = (w - q) * 128.0
     return np.array(out)
 
 
@@ -85,16 +88,16 @@ def test_slices_reconstruct_within_remainder_bound():
     rng = np.random.default_rng(7)
     for hi, lo, exact in _d_rows(rng, 20, 129):
         sd, S, _ = _d_slices(hi, lo)
-        assert np.abs(exact).max() <= 63 / 64 * sd
-        assert np.all(np.abs(S[:, 0]) <= 63) and np.all(np.abs(S[:, 1:]) <= 33)
-        rec = S @ (64.0 ** -np.arange(1, 5))
+        assert np.abs(exact).max() <= 127 / 128 * sd
+        assert np.all(np.abs(S[:, 0]) <= 127) and np.all(np.abs(S[:, 1:]) <= 64)
+        rec = S @ (128.0 ** -np.arange(1, 5))
         assert np.all(np.abs(exact / sd - rec) <= SLICE_REM)
     for _ in range(20):
         m = rng.standard_normal(129) * 10.0 ** rng.uniform(-4, 1)
         sm, S = _m_slices(m)
-        assert np.abs(m).max() <= 63 / 64 * sm
-        assert np.all(np.abs(S[:, 0]) <= 63) and np.all(np.abs(S[:, 1:]) <= 33)
-        assert np.all(np.abs(m / sm - S @ (64.0 ** -np.arange(1, 5))) <= SLICE_REM)
+        assert np.abs(m).max() <= 127 / 128 * sm
+        assert np.all(np.abs(S[:, 0]) <= 127) and np.all(np.abs(S[:, 1:]) <= 64)
+        assert np.all(np.abs(m / sm - S @ (128.0 ** -np.arange(1, 5))) <= SLICE_REM)
 
 
 def test_accumulators_exact_and_dropped_terms_bounded():
@@ -107,11 +110,11 @@ def test_accumulators_exact_and_dropped_terms_bounded():
             m = rng.standard_normal(D) * 10.0 ** rng.uniform(-3, 0)
             sm, Sm = _m_slices(m)
             kept = np.zeros(D)
-            for w in range(5):
-                prod = sum(Sd[:, q] * Sm[:, w - q] for q in range(max(0, w - 3), min(w, 3) + 1))
-                assert np.abs(prod).max() <= PER_K_MAX[w]
-                assert np.abs(prod).sum() < 2 ** 23
-                kept += prod * 64.0 ** -(w + 2)
+            for pairs, w, cap in ACCS:
+                prod = sum(Sd[:, a] * Sm[:, b] for a, b in pairs)
+                assert np.abs(prod).max() <= cap
+                assert np.abs(prod).sum() < 2 ** 24
+                kept += prod * 128.0 ** -(w + 2)
             dropped = np.abs(exact * m - kept * sd * sm)
             bound = SLICE_DROP * sd * sm + SLICE_REM * (sm * np.abs(exact) + sd * np.abs(m))
             assert np.all(dropped <= bound * (1 + 1e-9))
