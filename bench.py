@@ -229,7 +229,6 @@ def run_reference(args):
         return
     import oracle
     import workload
-    live = psso.psso_microbench(sptr_of(torch))   # measured pipe / latency peaks of this GPU
     cfg = workload.config(args.workload)
     p = cfg["problems"][0]
     threads = max(1, os.cpu_count() or 1)
