@@ -220,7 +220,8 @@ struct FitEpi {
     float acc, acc2, accE, rQ;
     __device__ void operator()(int c, const float (&tj)[32], const float (&em)[32])
     {
-        const int j0 = blockIdx.y * tc::SBN + 32 * c;
+        const int nt = tc::slice_tile_n(r->Jp);
+        const int j0 = nt * tc::SBN + 32 * c;
         float s = 0.f, s2 = 0.f, e = 0.f, eq = 0.f;
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
@@ -241,9 +242,9 @@ struct FitEpi {
         accE = __fadd_rn(accE, e);
         rQ = __fadd_rn(rQ, eq);
         if (c == tc::SBN / 32 - 1) {
-            const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
-            if (i < r->N && PSSO_CHK(blockIdx.y < (unsigned)r->nJt, CHK_TILE, blockIdx.y))
-                r->part[i * r->nJt + blockIdx.y] = make_float4(acc, acc2, accE, rQ);
+            const int64_t i = (int64_t)tc::slice_tile_m(r->Jp) * BM + threadIdx.x;
+            if (i < r->N && PSSO_CHK(nt < r->nJt, CHK_TILE, nt))
+                r->part[i * r->nJt + nt] = make_float4(acc, acc2, accE, rQ);
         }
     }
 };
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(128, 1)
     rot_gemm_fit(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ RotDev r)
 {
-    const int64_t i = (int64_t)blockIdx.x * BM + threadIdx.x;
+    const int64_t i = (int64_t)tc::slice_tile_m(r.Jp) * BM + threadIdx.x;
     FitEpi epi{&r,  base_fn(r.fn), r.D, i < r.N ? r.dscale[i] : 1.f, i < r.N ? r.dl1[i] : 0.f,
                tc::SLICE_DROP * (float)r.D, 0.f, 0.f, 0.f, 0.f};
     tc::GemmArgs a{r.Np, r.Jp, r.Kp, &r.ctl->status};
@@ -774,7 +775,7 @@ cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent
     const int wpb = 8;
     rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();
-    rot_gemm_fit<<<dim3(r.Np / BM, r.Jp / tc::SBN), 128, tc::S_SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
+    rot_gemm_fit<<<(unsigned)((long long)(r.Np / BM) * (r.Jp / tc::SBN)), 128, tc::S_SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
     mark();
     rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();

@@ -435,7 +435,13 @@ __device__ __forceinline__ void slice4_f64(double u, __nv_bfloat16 (&o)[SLICES])
     }
 }
 
-// The GEMM main loop of tile (blockIdx.x, blockIdx.y) over SLICES A planes
+// Tiles of the slice GEMM: a 1-D grid of (Np / BM) * (Jp / SBN) CTAs, the
+// column tile varying fastest, so that CTAs that run together share their A
+// slices through L2.
+__device__ __forceinline__ int slice_tile_m(int Jp) { return (int)(blockIdx.x / (unsigned)(Jp / SBN)); }
+__device__ __forceinline__ int slice_tile_n(int Jp) { return (int)(blockIdx.x % (unsigned)(Jp / SBN)); }
+
+// The GEMM main loop of tile (slice_tile_m, slice_tile_n) over SLICES A planes
 // [SLICES][Np][Kp] and B planes [SLICES][Jp][Kp] (Jp a multiple of SBN, Kp of
 // BK, Kp <= S_MAX_K).  The epilogue functor gets (column block c of 32,
 // t[32], em[32]) with t the joined accumulators and em the sum of the
@@ -452,7 +458,7 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * SBN;
+    const int m0 = slice_tile_m(a.Jp) * BM, n0 = slice_tile_n(a.Jp) * SBN;
     const int nkb = a.Kp / BK;
     const uint32_t sbase = smem_u32(smem);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
