@@ -609,10 +609,11 @@ def main():
 
     timed_launches = [0]
 
-    def timed_steps(h, steps, warm):
+    def timed_steps(h, steps, warm, gens=None):
+        gens = gens or t
         for _ in range(warm):
             psso.psso_reset(h)
-            psso.psso_run(h, t)
+            psso.psso_run(h, gens)
         psso.psso_sync(h)
         step_ms, kern_ms = [], []
         launches0 = psso.psso_stats(h)["launches"]
@@ -625,7 +626,7 @@ def main():
             e0.record(stream)
             psso.psso_reset(h)
             e1.record(stream)
-            psso.psso_run(h, t)
+            psso.psso_run(h, gens)
             e2.record(stream)
             e2.synchronize()
             step_ms.append(e0.elapsed_time(e2))
@@ -665,13 +666,19 @@ def main():
     if prec != "f64" and args.fp64_steps > 0:
         shape64, _ = tuned_shape("f64")
         h = psso.psso_create_ex(problems, "f64", stream=sptr, **shape64)
-        s64, k64 = timed_steps(h, args.fp64_steps, 1)
+        # a bounded sample where FP64 is slow (rotated swarms: GB300's FP64 rate):
+        # the first t64 generations, sized to about 3 s per step
+        g_probe = min(t, 10)
+        p_ms, _ = timed_steps(h, 1, 0, g_probe)
+        t64 = int(min(t, max(g_probe, 3000.0 / max(p_ms[0] / g_probe, 1e-6))))
+        s64, k64 = timed_steps(h, args.fp64_steps, 1, t64)
         b64 = psso.psso_best(h, 0)
         psso.psso_destroy(h)
-        v64 = upd_per_step * len(s64) / (sum(s64) / 1e3)
+        v64 = upd_per_step * (t64 / t) * len(s64) / (sum(s64) / 1e3)
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": sum(s64) / len(s64),
-                "kernel_ms": sum(k64) / len(k64), "speedup_f32_over_f64": value / world / v64,
-                "same_gbest": bool(b64[1] == best[1] and b64[0] == best[0])}
+                "kernel_ms": sum(k64) / len(k64), "generations": t64,
+                "speedup_f32_over_f64": value / world / v64,
+                "same_gbest": bool(b64[1] == best[1] and b64[0] == best[0]) if t64 == t else None}
 
     # --- opt-in gBest polish (workloads that name one) -------------------------------------
     polish = None
