@@ -256,16 +256,28 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
                 }
             }
             if (has) {
+                // the four terms of the chunk, one function dispatch per chunk
+                // (the switch inside the term is resolved at compile time)
+                auto terms = [&](auto fc) {
+                    constexpr int F = decltype(fc)::value;
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int j = 4 * c + m;
-                    if (j >= in.D) break;
-                    if (fn == FN_ROSENBROCK && m == 3 && lane == 31) {
-                        pend_j = j;
-                        pend_z = dv[3];
-                        continue;
+                    for (int m = 0; m < 4; ++m) {
+                        const int j = 4 * c + m;
+                        if (j >= in.D) break;
+                        if (F == FN_ROSENBROCK && m == 3 && lane == 31) {
+                            pend_j = j;
+                            pend_z = dv[3];
+                            continue;
+                        }
+                        sa.term(F, in, j, dv[m], m < 3 ? dv[(m + 1) & 3] : next);
                     }
-                    sa.term(fn, in, j, dv[m], m < 3 ? dv[(m + 1) & 3] : next);
+                };
+                switch (fn) {
+                case FN_SPHERE: terms(std::integral_constant<int, FN_SPHERE>()); break;
+                case FN_ELLIPSOID: terms(std::integral_constant<int, FN_ELLIPSOID>()); break;
+                case FN_RASTRIGIN: terms(std::integral_constant<int, FN_RASTRIGIN>()); break;
+                case FN_ROSENBROCK: terms(std::integral_constant<int, FN_ROSENBROCK>()); break;
+                default: terms(std::integral_constant<int, FN_ACKLEY>()); break;
                 }
             }
         }
