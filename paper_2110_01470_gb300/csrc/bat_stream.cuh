@@ -1,17 +1,22 @@
 // bat_stream.cuh -- streaming step kernel of the batched throughput pipeline
 // for wide rows (more than 128 variables, unrotated functions).
 //
-// One warp per particle walks its row one 32-chunk slice at a time: Eq. 2.1
-// for the slice (the same draws as the persistent kernel), the slice stored,
-// its fitness terms added to the lanes' running sums.  Registers hold one
-// slice instead of the whole row, so many more warps fit on an SM to hide the
-// row loads.  A lane meets its variables in ascending order, as in the
-// whole-row code, so the FP64 value keeps the oracle's summation order bit for
-// bit: the only term that needs the next slice -- Rosenbrock's last term of
-// lane 31, which needs the first variable of lane 0's next chunk -- is added
-// at the start of the next slice.  The FP32 value and its bound are those of
-// the whole-row FP32 path (same terms, same summation depth).  An accepted
-// row is copied to P by reading back the stored slices.
+// One warp per particle; the row is staged in the warp's shared memory and
+// processed in three passes:
+//   1. Eq. 2.1 slice by slice (32 chunks of 4 variables per slice, the same
+//      draws as the persistent kernel): the interval draw of every chunk,
+//      the selected source values into the staged row; a chunk with variables
+//      in the last interval (about a third of them) queues a request for its
+//      fresh-value block, and its staged values there hold the pBest value
+//      for the row-equality test;
+//   2. the queued fresh-value blocks, 32 per round, one per lane: the Philox
+//      work of the last branch is paid only for the chunks that need it;
+//   3. slice by slice again: the staged row stored to X and its fitness terms
+//      added to the lanes' running sums.
+// A lane meets its variables in ascending order, as in the whole-row code, so
+// the FP64 value keeps the oracle's summation order bit for bit; the FP32
+// value and its bound are those of the whole-row FP32 path (same terms, same
+// summation depth).  An accepted row is copied to P from the staged row.
 #pragma once
 #include <type_traits>
 
@@ -153,15 +158,28 @@ struct StreamAcc<true> {
     }
 };
 
+// Shared memory of one warp: the staged row (1024 positions) and the queue of
+// fresh-value requests (chunk | mask << 8, at most 256).
+constexpr int STREAM_ROW = 1024;
+template <class Pos>
+__host__ __device__ constexpr size_t stream_smem_per_warp()
+{
+    return (size_t)STREAM_ROW * sizeof(Pos) + 256 * sizeof(uint32_t);
+}
+
 template <class Pos, bool F32R>
 __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
 {
     using Val = typename std::conditional<F32R, float, double>::type;
+    extern __shared__ __align__(16) unsigned char bs_smem[];
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
     const int64_t nwarps = wpb * gridDim.x;
     const int64_t g = *p.gen;
     const uint32_t gg = (uint32_t)g;
+    Pos* const row = reinterpret_cast<Pos*>(bs_smem + (threadIdx.x >> 5) * stream_smem_per_warp<Pos>());
+    uint32_t* const req = reinterpret_cast<uint32_t*>(row + STREAM_ROW);
+    const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t gid = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); gid < p.total; gid += nwarps) {
         int lo = 0, hi = p.n_ids - 1;
         while (lo < hi) {
@@ -172,116 +190,126 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
         const int k = __ldg(p.ids + lo);
         const int64_t i = gid - __ldg(p.first + lo);
         const InstDev& d = p.inst[k];
-        if (!PSSO_CHK(i >= 0 && i < d.N, CHK_BAT_ROW, gid)) continue;
+        if (!PSSO_CHK(i >= 0 && i < d.N && d.Dp <= STREAM_ROW, CHK_BAT_ROW, gid)) continue;
         const Hot in = hot_of(d);
         const int fn = in.fn;
         const int nq = (in.nchunks + 31) >> 5;
+        const uint32_t ii = (uint32_t)i + in.i_base;
         Pos* xr = static_cast<Pos*>(d.X) + i * in.Dp;
         Pos* prow = static_cast<Pos*>(d.P) + i * in.Dp;
         const Pos* gs = static_cast<const Pos*>(d.gbrow);
-        const uint32_t ctr3r = TAG_RHO | (in.sid << 8), ctr3f = TAG_FRESH | (in.sid << 8);
-        StreamAcc<F32R> sa;
+        const uint32_t ctr3r = TAG_RHO | (in.sid << 8);
         bool eqp = true;
-        Val pend_z = Val(0);
-        int pend_j = -1;               // lane 31: Rosenbrock term waiting for the next slice
+        __syncwarp();     // the previous row's staged values are consumed
+
+        // ---- pass 1: the interval draws; fresh-value requests --------------------------
+        int nreq = 0;     // warp-uniform
         for (int q = 0; q < nq; ++q) {
             const int c = lane + 32 * q;
-            const bool has = c < in.nchunks;
-            Pos x[4] = {Pos(0), Pos(0), Pos(0), Pos(0)};
-            if (has) {
+            uint32_t nf = 0;
+            if (c < in.nchunks) {
                 const int nvalid = min(4, in.D - 4 * c);
                 const uint32_t valid = (1u << nvalid) - 1u;
+                Pos x[4] = {Pos(0), Pos(0), Pos(0), Pos(0)};
                 if (g == 0) {
-                    fresh_chunk(x, valid, (uint32_t)c, (uint32_t)i + in.i_base, 0u, TAG_INIT, in);
+                    fresh_chunk(x, valid, (uint32_t)c, ii, 0u, TAG_INIT, in);
                 } else {
-                    // the slice's loads first: the draws below do not depend on
-                    // them and cover their latency
                     Pos xo[4], po[4], go[4];
                     // xo: the third interval's source, go: the first's (Eq. 2.1 as printed
                     // swaps them: keep x first, gBest third)
                     ld4((in.order ? gs : xr) + 4 * c, xo);
                     ld4(prow + 4 * c, po);
                     ld4((in.order ? xr : gs) + 4 * c, go);
-                    const uint4 rb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3r), in.k0, in.k1);
-                    uint4 fb = make_uint4(0u, 0u, 0u, 0u);
-                    if (sizeof(Pos) == 4)
-                        fb = philox10(make_uint4((uint32_t)c, (uint32_t)i + in.i_base, gg, ctr3f), in.k0, in.k1);
-                    uint32_t nf = 0;
+                    const uint4 rb = philox10(make_uint4((uint32_t)c, ii, gg, ctr3r), in.k0, in.k1);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const uint32_t r = word_of(rb, m);
                         const bool lg = (r < in.Tg32) || (in.tfull & 1u);
                         const bool lp = (r < in.Tp32) || (in.tfull & 2u);
                         const bool lw = (r < in.Tw32) || (in.tfull & 4u);
-                        x[m] = lg ? go[m] : lp ? po[m] : xo[m];
+                        // a variable of the last interval holds its pBest value until
+                        // pass 2 compares and replaces it
+                        x[m] = lg ? go[m] : (lp || !lw) ? po[m] : xo[m];
                         if (!lw) nf |= 1u << m;
                     }
                     nf &= valid;
-                    if (nf) {
-                        if constexpr (sizeof(Pos) == 4) {
-#pragma unroll
-                            for (int m = 0; m < 4; ++m)
-                                if (nf & (1u << m)) x[m] = (Pos)fresh_f32(word_of(fb, m), in);
-                        } else {
-                            fresh_chunk(x, nf, (uint32_t)c, (uint32_t)i + in.i_base, gg, TAG_FRESH, in);
-                        }
-                    }
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         if (m >= nvalid) x[m] = Pos(0);
-                        eqp = eqp && same_bits(x[m], po[m]);
+                        if (!(nf & (1u << m))) eqp = eqp && same_bits(x[m], po[m]);
                     }
                 }
-                st4(xr + 4 * c, x);
+                st4(row + 4 * c, x);
             }
-            // fitness terms of the slice (the shift is padded to Dp values)
-            Val dv[4], ov[4] = {Val(0), Val(0), Val(0), Val(0)};
-            if (has) {
-                if constexpr (F32R) ld4(in.o32 + 4 * c, ov);
-                else ld4(in.o64 + 4 * c, ov);
+            const unsigned want = __ballot_sync(0xffffffffu, nf != 0u);
+            if (nf) req[nreq + __popc(want & lt_mask)] = (uint32_t)c | (nf << 8);
+            nreq += __popc(want);
+        }
+        __syncwarp();
+
+        // ---- pass 2: the queued fresh-value blocks, one per lane and round ------------------
+        for (int base = 0; base < nreq; base += 32) {
+            const int e = base + lane;
+            if (e < nreq) {
+                const uint32_t rq = req[e];
+                const uint32_t c = rq & 0xffu, nf = rq >> 8;
+                Pos fv[4], pv[4];
+                ld4(row + 4 * c, pv);     // the pBest values held in pass 1
+                fresh_chunk(fv, nf, c, ii, gg, TAG_FRESH, in);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if (nf & (1u << m)) {
+                        eqp = eqp && same_bits(fv[m], pv[m]);
+                        pv[m] = fv[m];
+                    }
+                st4(row + 4 * c, pv);
             }
+        }
+        __syncwarp();
+
+        // ---- pass 3: X and the fitness terms --------------------------------------------------
+        StreamAcc<F32R> sa;
+        for (int q = 0; q < nq; ++q) {
+            const int c = lane + 32 * q;
+            if (c >= in.nchunks) continue;
+            Pos x[4];
+            ld4(row + 4 * c, x);
+            st4(xr + 4 * c, x);
+            // fitness terms of the chunk (the shift is padded to Dp values)
+            Val dv[4], ov[4];
+            if constexpr (F32R) ld4(in.o32 + 4 * c, ov);
+            else ld4(in.o64 + 4 * c, ov);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int j = 4 * c + m;
-                if constexpr (F32R) dv[m] = (has && j < in.D) ? __fsub_rn((float)x[m], ov[m]) : 0.f;
-                else dv[m] = (has && j < in.D) ? __dsub_rn((double)x[m], ov[m]) : 0.0;
+                if constexpr (F32R) dv[m] = (j < in.D) ? __fsub_rn((float)x[m], ov[m]) : 0.f;
+                else dv[m] = (j < in.D) ? __dsub_rn((double)x[m], ov[m]) : 0.0;
             }
+            // Rosenbrock's last term of the chunk needs the next chunk's first variable
             Val next = Val(0);
-            if (fn == FN_ROSENBROCK) {
-                next = __shfl_down_sync(0xffffffffu, dv[0], 1);
-                const Val first0 = __shfl_sync(0xffffffffu, dv[0], 0);
-                if (lane == 31 && pend_j >= 0) {
-                    sa.term(fn, in, pend_j, pend_z, first0);
-                    pend_j = -1;
-                }
+            if (fn == FN_ROSENBROCK && 4 * c + 4 < in.D) {
+                if constexpr (F32R) next = __fsub_rn((float)row[4 * c + 4], __ldg(in.o32 + 4 * c + 4));
+                else next = __dsub_rn((double)row[4 * c + 4], __ldg(in.o64 + 4 * c + 4));
             }
-            if (has) {
-                // the four terms of the chunk, one function dispatch per chunk
-                // (the switch inside the term is resolved at compile time)
-                auto terms = [&](auto fc) {
-                    constexpr int F = decltype(fc)::value;
+            // the four terms of the chunk, one function dispatch per chunk
+            // (the switch inside the term is resolved at compile time)
+            auto terms = [&](auto fc) {
+                constexpr int F = decltype(fc)::value;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int j = 4 * c + m;
-                        if (j >= in.D) break;
-                        if (F == FN_ROSENBROCK && m == 3 && lane == 31) {
-                            pend_j = j;
-                            pend_z = dv[3];
-                            continue;
-                        }
-                        sa.term(F, in, j, dv[m], m < 3 ? dv[(m + 1) & 3] : next);
-                    }
-                };
-                switch (fn) {
-                case FN_SPHERE: terms(std::integral_constant<int, FN_SPHERE>()); break;
-                case FN_ELLIPSOID: terms(std::integral_constant<int, FN_ELLIPSOID>()); break;
-                case FN_RASTRIGIN: terms(std::integral_constant<int, FN_RASTRIGIN>()); break;
-                case FN_ROSENBROCK: terms(std::integral_constant<int, FN_ROSENBROCK>()); break;
-                default: terms(std::integral_constant<int, FN_ACKLEY>()); break;
+                for (int m = 0; m < 4; ++m) {
+                    const int j = 4 * c + m;
+                    if (j >= in.D) break;
+                    sa.term(F, in, j, dv[m], m < 3 ? dv[m + 1] : next);
                 }
+            };
+            switch (fn) {
+            case FN_SPHERE: terms(std::integral_constant<int, FN_SPHERE>()); break;
+            case FN_ELLIPSOID: terms(std::integral_constant<int, FN_ELLIPSOID>()); break;
+            case FN_RASTRIGIN: terms(std::integral_constant<int, FN_RASTRIGIN>()); break;
+            case FN_ROSENBROCK: terms(std::integral_constant<int, FN_ROSENBROCK>()); break;
+            default: terms(std::integral_constant<int, FN_ACKLEY>()); break;
             }
         }
-        // lane 31's pending term has no next slice: it is the row's last variable (no term)
         const bool same_row = (g > 0) && __all_sync(0xffffffffu, eqp);
         bool accept, wstate = true, undecided = false;
         double f64v = 0.0;
@@ -330,10 +358,9 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
             }
         }
         if (accept && wstate) {
-            __syncwarp();
             for (int c = lane; c < in.nchunks; c += 32) {
                 Pos v[4];
-                ld4(xr + 4 * c, v);
+                ld4(row + 4 * c, v);
                 st4(prow + 4 * c, v);
             }
             if (lane == 0) {
@@ -356,8 +383,14 @@ __global__ void __launch_bounds__(256, 4) bat_stream(const BatParams p)
 template <class Pos, bool F32R>
 inline cudaError_t bat_stream_entry(int op, const BatParams* p, int grid, int block, cudaStream_t s, int* out)
 {
-    if (op == 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_stream<Pos, F32R>, block, 0);
-    bat_stream<Pos, F32R><<<grid, block, 0, s>>>(*p);
+    const size_t smem = (size_t)(block >> 5) * stream_smem_per_warp<Pos>();
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(bat_stream<Pos, F32R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (op == 3) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bat_stream<Pos, F32R>, block, smem);
+    bat_stream<Pos, F32R><<<grid, block, smem, s>>>(*p);
     return cudaGetLastError();
 }
 
