@@ -294,7 +294,7 @@ def job_rate(units_per_step, steps, world, max_total_ms):
 TRAFFIC = {
     ("rot_gemm_fit", "rotated_d1000"): ("9acd2b026714429a", 75.648256e6 + 3.735552e6),
     ("sso_generations", "rastrigin_d100"): ("c5a611e6e84c4e41", 1.407488e6 + 0.055552e6),
-    ("bat_stream", "batched_512"): ("4fcbb2ebf8f85287", 685.001728e6 + 1195.711e6),
+    ("bat_stream", "batched_512"): ("b96e79894cdf97df", 668.860928e6 + 913.625856e6),
 }
 _COMMON = ["sso_common.cuh", "devmath.cuh", "psso_internal.h", "checked.cuh"]
 KERNEL_SOURCES = {
