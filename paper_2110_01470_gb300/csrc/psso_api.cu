@@ -99,6 +99,11 @@ struct BatHost {
     void* mem = nullptr;
     cudaGraphExec_t graph1 = nullptr, graphG = nullptr;
     static constexpr int GRAPH_GENS = 16;
+    // classes after the first run on side streams (parallel branches of the
+    // captured graphs): they touch disjoint swarms
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
 };
 
 }  // namespace
@@ -582,17 +587,33 @@ psso_status setup_tc(psso_ctx* h, size_t k)
 cudaError_t enqueue_bat_generation(psso_ctx* h, cudaStream_t s, cudaEvent_t* ev = nullptr)
 {
     const InstDev* inst = reinterpret_cast<const InstDev*>(h->arena + h->off_instdev);
+    BatHost& B = h->bat;
+    auto step = [&](const BatHost::Class& c, cudaStream_t st) {
+        BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, B.gen, B.cnt};
+        return c.stream ? bat_call(h->variant, 3, 2, &p, c.grid, 256, st, nullptr)
+                        : bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, st, nullptr);
+    };
     int q = 0;
     if (ev) cudaEventRecord(ev[q++], s);
-    for (const auto& c : h->bat.classes) {
-        BatParams p{inst, c.ids, c.first, c.n, c.G, c.total, h->bat.gen, h->bat.cnt};
-        const cudaError_t e = c.stream ? bat_call(h->variant, 3, 2, &p, c.grid, 256, s, nullptr)
-                                       : bat_call(h->variant, c.mc_index, 0, &p, c.grid, 256, s, nullptr);
-        if (e != cudaSuccess) return e;
+    // With per-kernel events (psso_time_kernels) the classes run one after another.
+    const bool branch = !ev && B.side.size() + 1 == B.classes.size() && B.classes.size() > 1;
+    cudaError_t e = cudaSuccess;
+    if (branch) e = cudaEventRecord(B.fork, s);
+    for (size_t k = 0; k < B.classes.size() && e == cudaSuccess; ++k) {
+        cudaStream_t st = s;
+        if (branch && k > 0) {
+            st = B.side[k - 1];
+            e = cudaStreamWaitEvent(st, B.fork, 0);
+            if (e != cudaSuccess) break;
+        }
+        e = step(B.classes[k], st);
+        if (e == cudaSuccess && branch && k > 0) e = cudaEventRecord(B.join[k - 1], st);
         if (ev) cudaEventRecord(ev[q++], s);
     }
-    const cudaError_t e =
-        launch_bat_argmin(h->variant, inst, h->bat.all_ids, h->bat.n_all, h->bat.gen, h->bat.cnt, s);
+    for (size_t k = 0; branch && k + 1 < B.classes.size() && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(s, B.join[k], 0);
+    if (e != cudaSuccess) return e;
+    e = launch_bat_argmin(h->variant, inst, B.all_ids, B.n_all, B.gen, B.cnt, s);
     if (ev) cudaEventRecord(ev[q++], s);
     return e;
 }
@@ -671,6 +692,18 @@ psso_status setup_bat(psso_ctx* h)
     B.gen = reinterpret_cast<long long*>(base + ogen);
     CUDA_TRY(cudaMemcpy(B.mem, host.data(), bytes, cudaMemcpyHostToDevice));
     h->h2d += (int64_t)bytes;
+    // side streams of the classes after the first (released by psso_destroy)
+    if (B.classes.size() > 1) {
+        CUDA_TRY(cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
+        for (size_t k = 1; k < B.classes.size(); ++k) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t je = nullptr;
+            CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            B.side.push_back(st);
+            CUDA_TRY(cudaEventCreateWithFlags(&je, cudaEventDisableTiming));
+            B.join.push_back(je);
+        }
+    }
     // graphs of 1 and GRAPH_GENS generations, captured on a private stream
     cudaStream_t cs;
     CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1418,6 +1451,9 @@ void psso_destroy(psso_handle h)
     if (h->bat.graph1) cudaGraphExecDestroy(h->bat.graph1);
     if (h->bat.graphG) cudaGraphExecDestroy(h->bat.graphG);
     if (h->bat.mem) cudaFree(h->bat.mem);
+    for (auto st : h->bat.side) cudaStreamDestroy(st);
+    for (auto je : h->bat.join) cudaEventDestroy(je);
+    if (h->bat.fork) cudaEventDestroy(h->bat.fork);
     if (h->amem) cudaFree(h->amem);
     delete h;
 }
