@@ -136,6 +136,12 @@ struct psso_ctx {
     // asynchronous flow (Alg. 1): one cooperative kernel; its scratch and control words
     bool async = false;
     bool shard = false;           // created by psso_create_shard
+    // tensor-pipeline swarms run on their own streams after the persistent
+    // kernel in stream order (never beside it: its blocks wait on one another),
+    // concurrently with one another and with the batched graphs
+    std::vector<cudaStream_t> tc_side;
+    std::vector<cudaEvent_t> tc_join;
+    cudaEvent_t tc_fork = nullptr;
     void* amem = nullptr;
     AsyncCtl* actl = nullptr;
     void* axs = nullptr;
@@ -499,11 +505,40 @@ psso_status launch(psso_ctx* h, int64_t g_begin, int64_t g_end)
         for (; count > 0; --count) CUDA_TRY(cudaGraphLaunch(h->bat.graph1, h->stream));
         h->launches += 1 + (int64_t)(h->bat.classes.size() + 2) * (g_end - g_begin + 1);
     }
+    // tensor-pipeline swarms: forked after everything above in stream order,
+    // one side stream each (the handle's stream when there is no side stream)
+    const bool fork = !h->tc_side.empty();
+    if (fork) CUDA_TRY(cudaEventRecord(h->tc_fork, h->stream));
+    size_t j = 0;
     for (auto& I : h->inst) {
         if (!I.tc) continue;
-        CUDA_TRY(rot::set_generation(I.rh, g_begin, h->stream));
-        CUDA_TRY(rot::run_generations(I.rh, g_end - g_begin + 1, h->stream));
+        cudaStream_t st = fork ? h->tc_side[j] : h->stream;
+        if (fork) CUDA_TRY(cudaStreamWaitEvent(st, h->tc_fork, 0));
+        CUDA_TRY(rot::set_generation(I.rh, g_begin, st));
+        CUDA_TRY(rot::run_generations(I.rh, g_end - g_begin + 1, st));
+        if (fork) CUDA_TRY(cudaEventRecord(h->tc_join[j], st));
         h->launches += 1 + rot::KERNELS_PER_GENERATION * (g_end - g_begin + 1);
+        ++j;
+    }
+    for (size_t q = 0; fork && q < h->tc_join.size(); ++q) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->tc_join[q], 0));
+    return PSSO_OK;
+}
+
+// Side streams of the tensor-pipeline swarms: one per swarm when there are
+// two or more of them (released by psso_destroy).
+psso_status setup_tc_streams(psso_ctx* h)
+{
+    size_t n = 0;
+    for (const auto& I : h->inst) n += I.tc ? 1 : 0;
+    if (n < 2) return PSSO_OK;
+    CUDA_TRY(cudaEventCreateWithFlags(&h->tc_fork, cudaEventDisableTiming));
+    for (size_t q = 0; q < n; ++q) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t je = nullptr;
+        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        h->tc_side.push_back(st);
+        CUDA_TRY(cudaEventCreateWithFlags(&je, cudaEventDisableTiming));
+        h->tc_join.push_back(je);
     }
     return PSSO_OK;
 }
@@ -1025,6 +1060,8 @@ psso_status create_impl(const psso_problem* problems, int32_t count, const psso_
     if (st != PSSO_OK) return cleanup_fail(st);
     st = setup_async(h);
     if (st != PSSO_OK) return cleanup_fail(st);
+    st = setup_tc_streams(h);
+    if (st != PSSO_OK) return cleanup_fail(st);
     st = launch(h, 0, 0);
     if (st != PSSO_OK) return cleanup_fail(st);
     for (auto& I : h->inst) h->evals += I.pr.N;
@@ -1452,6 +1489,9 @@ void psso_destroy(psso_handle h)
     if (h->bat.graphG) cudaGraphExecDestroy(h->bat.graphG);
     if (h->bat.mem) cudaFree(h->bat.mem);
     for (auto st : h->bat.side) cudaStreamDestroy(st);
+    for (auto st : h->tc_side) cudaStreamDestroy(st);
+    for (auto je : h->tc_join) cudaEventDestroy(je);
+    if (h->tc_fork) cudaEventDestroy(h->tc_fork);
     for (auto je : h->bat.join) cudaEventDestroy(je);
     if (h->bat.fork) cudaEventDestroy(h->bat.fork);
     if (h->amem) cudaFree(h->amem);
