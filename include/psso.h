@@ -170,7 +170,10 @@ typedef struct {
                                    0 = auto (swarms with N >= 128 and D >= 32 run
                                    each generation as a kernel sequence around a
                                    tcgen05 tensor-core GEMM for z = M (x - o));
-                                   1 = always; -1 = never (per-particle kernel)     */
+                                   1 = always; -1 = never (per-particle kernel).
+                                   The GEMM is exact for D <= 1023: a swarm with
+                                   D = 1024 runs the per-particle kernel (auto) or
+                                   fails with PSSO_ERR_UNSUPPORTED (always)        */
     int32_t batch_stream;       /* handles of many swarms: 0 = auto (16 or more
                                    swarms that are not on the tensor-core pipeline
                                    run each generation as one kernel per row-width

@@ -558,7 +558,8 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     r.Jp = (D + tc::SBN - 1) / tc::SBN * tc::SBN;
     r.Kp = (D + tc::BK - 1) / tc::BK * tc::BK;
     r.nJt = r.Jp / tc::SBN;
-    if (r.Kp > tc::S_MAX_K) return fail(PSSO_ERR_UNSUPPORTED, "tensor pipeline: D above the slice GEMM's exact range");
+    if (r.Kp > tc::S_MAX_K || D > tc::S_MAX_D)
+        return fail(PSSO_ERR_UNSUPPORTED, "tensor pipeline: D above the slice GEMM's exact range");
     size_t off = 0;
     auto take = [&](size_t bytes) {
         off = align_up(off, 256);
@@ -608,6 +609,7 @@ psso_status setup_tc(psso_ctx* h, size_t k)
     R.z64_grid = 2 * prop.multiProcessorCount;
     R.z32_grid = 8 * prop.multiProcessorCount;
     R.fix_grid = prop.multiProcessorCount;
+    R.gemm_grid = (int)std::min<long long>((long long)(r.Np / tc::BM) * r.nJt, prop.multiProcessorCount);
     if (!tc::make_tmap_bf16(&R.tmA, r.A, r.Kp, tc::SLICES * r.Np) ||
         !tc::make_tmap_bf16(&R.tmB, R.B, r.Kp, tc::SLICES * r.Jp, tc::SBN))
         return fail(PSSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tensor-core operands");
@@ -927,7 +929,8 @@ psso_status create_impl(const psso_problem* problems, int32_t count, const psso_
         if (rot) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
         I.tc = h->precision == PSSO_PREC_F32_RECHECK && rot &&
-               (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32));
+               (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32)) &&
+               I.pr.D <= tc::S_MAX_D;
     }
     {
         int n_plain = 0;

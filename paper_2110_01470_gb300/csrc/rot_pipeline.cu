@@ -216,11 +216,22 @@ __device__ __forceinline__ void term32(int fn, float zt, float ez, const float* 
 struct FitEpi {
     const RotDev* r;
     int fn, D;
-    float ds, dl1, drop;          // s_d, sum |d_k|, SLICE_DROP * D
+    float drop;                   // SLICE_DROP * D
+    // the current tile and row: particle i, column tile nt, s_d, sum |d_k|
+    int64_t i;
+    int nt;
+    float ds, dl1;
     float acc, acc2, accE, rQ;
+    __device__ void tile(int tm, int tn, int row)
+    {
+        i = (int64_t)tm * BM + row;
+        nt = tn;
+        ds = i < r->N ? r->dscale[i] : 1.f;
+        dl1 = i < r->N ? r->dl1[i] : 0.f;
+        acc = acc2 = accE = rQ = 0.f;
+    }
     __device__ void operator()(int c, const float (&tj)[32], const float (&em)[32])
     {
-        const int nt = tc::slice_tile_n(r->Jp);
         const int j0 = nt * tc::SBN + 32 * c;
         float s = 0.f, s2 = 0.f, e = 0.f, eq = 0.f;
 #pragma unroll
@@ -242,22 +253,20 @@ struct FitEpi {
         accE = __fadd_rn(accE, e);
         rQ = __fadd_rn(rQ, eq);
         if (c == tc::SBN / 32 - 1) {
-            const int64_t i = (int64_t)tc::slice_tile_m(r->Jp) * BM + threadIdx.x;
             if (i < r->N && PSSO_CHK(nt < r->nJt, CHK_TILE, nt))
                 r->part[i * r->nJt + nt] = make_float4(acc, acc2, accE, rQ);
         }
     }
 };
 
-__global__ void __launch_bounds__(128, 1)
+// Persistent: one CTA per SM (at most one per tile), tiles in grid-stride order.
+__global__ void __launch_bounds__(tc::S_THREADS, 1)
     rot_gemm_fit(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ RotDev r)
 {
-    const int64_t i = (int64_t)tc::slice_tile_m(r.Jp) * BM + threadIdx.x;
-    FitEpi epi{&r,  base_fn(r.fn), r.D, i < r.N ? r.dscale[i] : 1.f, i < r.N ? r.dl1[i] : 0.f,
-               tc::SLICE_DROP * (float)r.D, 0.f, 0.f, 0.f, 0.f};
+    FitEpi epi{&r, base_fn(r.fn), r.D, tc::SLICE_DROP * (float)r.D};
     tc::GemmArgs a{r.Np, r.Jp, r.Kp, &r.ctl->status};
-    tc::gemm_tile_sliced(&tmA, &tmB, a, epi);
+    tc::gemm_sliced_persistent(&tmA, &tmB, a, epi);
 }
 
 // ---- 3. FP32 decisions ------------------------------------------------------------
@@ -775,7 +784,7 @@ cudaError_t enqueue_generation_timed(const RotHost& h, cudaStream_t s, cudaEvent
     const int wpb = 8;
     rot_update<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();
-    rot_gemm_fit<<<(unsigned)((long long)(r.Np / BM) * (r.Jp / tc::SBN)), 128, tc::S_SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
+    rot_gemm_fit<<<h.gemm_grid, tc::S_THREADS, tc::S_SMEM_BYTES, s>>>(h.tmA, h.tmB, r);
     mark();
     rot_decide<<<(N + wpb - 1) / wpb, 32 * wpb, 0, s>>>(r);
     mark();

@@ -61,6 +61,7 @@ struct RotHost {
     const double* M64;
     long long N;
     int z64_grid, z32_grid, fix_grid;
+    int gemm_grid;                 // persistent GEMM: min(tiles, SMs)
     void* mem;                     // the one allocation holding the buffers above
     size_t mem_bytes;
     cudaGraphExec_t graph1, graphG;  // one generation / GRAPH_GENS generations

@@ -358,53 +358,62 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, int Kp, int rows, int bo
 // Exact integer-slice GEMM (the tensor pipeline's rotation).
 //
 // Each operand row is scaled by a power of two s (s_d per particle, s_M per
-// output j) such that every entry satisfies |v| <= 127/128 s, and the exact
-// value (d = x - o as a float pair, M from its FP64 copy) is written as four
-// 7-bit integer slices,
+// output j) such that every entry satisfies |v| < s / 2, and the exact value
+// (d = x - o as a float pair, M from its FP64 copy) is written as four 7-bit
+// integer slices,
 //     v = s (V0 2^-7 + V1 2^-14 + V2 2^-21 + V3 2^-28 + r),
-// |V0| <= 127, |V1..V3| <= 64, |r| <= 1.01 2^-29 (successive round-to-nearest
-// with exact steps, slicers below).  The slice products of weight
-// w = s + t <= 3 are accumulated in six accumulators, products of equal
-// weight sharing one as far as exactness allows:
-//     acc0: D0 M0        acc1: D0 M1 + D1 M0     acc2: D0 M2 + D2 M0
-//     acc3: D1 M1        acc4: D0 M3 + D3 M0     acc5: D1 M2 + D2 M1
-// (ten MMAs per K step).  Every product is an integer; per k an accumulator
-// gains at most 16256 (acc0 16129, acc3 4096, acc5 8192), so for K <= 1024
-// every partial sum stays below 2^24: an FP32 accumulator represents all of
-// them exactly, and the accumulation is exact whatever the MMA datapath's
-// alignment and rounding (24 bits suffice).  The products of weight 4 .. 6
-// and the remainders r are dropped and bounded: per k,
+// |V0..V3| <= 64, |r| <= 1.01 2^-29 (successive round-to-nearest with exact
+// steps, slicers below).  The slice products of weight w = s + t <= 3 are
+// accumulated in four accumulators, one per weight:
+//     acc0: D0 M0                        acc1: D0 M1 + D1 M0
+//     acc2: D0 M2 + D1 M1 + D2 M0        acc3: D0 M3 + D1 M2 + D2 M1 + D3 M0
+// (ten MMAs per K step).  Every product is an integer of magnitude at most
+// 64^2 = 4096, so per k an accumulator gains at most 4 * 4096 = 16384; for
+// D <= 1023 nonzero k every partial sum stays below 2^24 in magnitude, an FP32
+// accumulator represents all of them exactly, and the accumulation is exact
+// whatever the MMA datapath's alignment and rounding (24 bits suffice).  The
+// products of weight 4 .. 6 and the remainders r are dropped and bounded: per k,
 //     s_d s_M SLICE_DROP + SLICE_REM (s_M |d_k| + s_d |M_jk|).
 // The epilogue joins the accumulators in FP32 from the smallest weight up,
-// t = acc0 + 2^-7 acc1 + 2^-14 (acc2 + acc3) + 2^-21 (acc4 + acc5) (five
-// rounded operations), and z = 2^-14 s_d s_M t exactly.
+// t = acc0 + 2^-7 acc1 + 2^-14 acc2 + 2^-21 acc3 (three rounded operations),
+// and z = 2^-14 s_d s_M t exactly.
+//
+// The kernel is persistent and warp-specialised: one CTA per SM walks the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 issues the TMA copies
+// (running ahead into the next tile while the current one computes), warp 1
+// issues the MMAs and owns the tensor memory, warps 2..5 run the epilogue.
+// Tensor memory holds two accumulator sets of 4 x 64 columns, so the
+// epilogue of one tile overlaps the MMAs of the next.
 constexpr int SBN = 64;                                     // output columns per tile
 constexpr int SLICES = 4;
-constexpr int SACC = 6;                                     // accumulators
+constexpr int SACC = 4;                                     // accumulators (one per weight)
 constexpr int SPAIRS = 10;                                  // MMAs per K step
 constexpr int S_A_BYTES = BM * BK * 2;                      // 16 KiB
 constexpr int S_B_BYTES = SBN * BK * 2;                     // 8 KiB
 constexpr int S_STAGE_BYTES = SLICES * (S_A_BYTES + S_B_BYTES);   // 96 KiB
 constexpr int S_SMEM_BYTES = STAGES * S_STAGE_BYTES + 1024;
-constexpr int S_TMEM_COLS = 512;                            // six accumulators of 64 columns (a power of two)
-constexpr int S_MAX_K = 1024;                               // exactness of the accumulators
+constexpr int S_ACC_COLS = SACC * SBN;                      // 256 columns per accumulator set
+constexpr int S_TMEM_COLS = 2 * S_ACC_COLS;                 // two sets (a power of two)
+constexpr int S_THREADS = 192;                              // TMA warp, MMA warp, four epilogue warps
+constexpr int S_MAX_K = 1024;                               // padded K extent (D <= 1023 for exactness)
+constexpr int S_MAX_D = 1023;
 // weight 4..6: 3 * 64^2 * 2^-42 + 2 * 64^2 * 2^-49 + 64^2 * 2^-56, and 3 r^2
 constexpr float SLICE_DROP = 3.04f * 0x1p-30f;              // per k, units of s_d s_M
 constexpr float SLICE_REM = 1.01f * 0x1p-29f;               // per k, of s_M |d_k| + s_d |M_jk|
 
 // Power-of-two scale s of a row with max |v| <= vmax (1 + 2^-22): every entry
-// satisfies |v| <= 127/128 s (s = 1 if vmax is 0).
+// satisfies |v| < s / 2 (s = 1 if vmax is 0).
 __host__ __device__ inline float slice_scale(float vmax)
 {
     if (!(vmax > 0.f)) return 1.f;
     int e = 0;
-    const float m = vmax * (128.f / 127.f) * (1.f + 0x1p-20f);   // rounded up
+    const float m = vmax * 2.f * (1.f + 0x1p-20f);                 // rounded up
     (void)frexpf(m, &e);                                            // m < 2^e
     return ldexpf(1.f, e);
 }
 
-// The four slices of u = u_hi + u_lo (an exact float pair, |u| <= 127/128)
-// as BF16 integers.  Each step keeps the rest exactly as a float pair: the
+// The four slices of u = u_hi + u_lo (an exact float pair, |u| < 1/2) as
+// BF16 integers.  Each step keeps the rest exactly as a float pair: the
 // rounded-off part of the high word is exact, a TwoSum renormalises, and the
 // scaling by 128 is exact.  The rest after four slices is within 1.01 2^-29.
 __device__ __forceinline__ void slice4_pair(float u_hi, float u_lo, __nv_bfloat16 (&o)[SLICES])
@@ -413,7 +422,7 @@ __device__ __forceinline__ void slice4_pair(float u_hi, float u_lo, __nv_bfloat1
 #pragma unroll
     for (int q = 0; q < SLICES; ++q) {
         const float iq = rintf(wh);
-        o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 127
+        o[q] = __float2bfloat16_rn(iq);              // an integer of magnitude <= 64
         const float r = __fsub_rn(wh, iq);           // exact
         const float s = __fadd_rn(r, wl);            // TwoSum(r, wl)
         const float bb = __fsub_rn(s, r);
@@ -423,7 +432,7 @@ __device__ __forceinline__ void slice4_pair(float u_hi, float u_lo, __nv_bfloat1
     }
 }
 
-// The same for an FP64 value u (|u| <= 127/128): the steps are exact in FP64.
+// The same for an FP64 value u (|u| < 1/2): the steps are exact in FP64.
 __device__ __forceinline__ void slice4_f64(double u, __nv_bfloat16 (&o)[SLICES])
 {
     double w = __dmul_rn(u, 128.0);
@@ -435,46 +444,61 @@ __device__ __forceinline__ void slice4_f64(double u, __nv_bfloat16 (&o)[SLICES])
     }
 }
 
-// Tiles of the slice GEMM: a 1-D grid of (Np / BM) * (Jp / SBN) CTAs, the
-// column tile varying fastest, so that CTAs that run together share their A
-// slices through L2.
-__device__ __forceinline__ int slice_tile_m(int Jp) { return (int)(blockIdx.x / (unsigned)(Jp / SBN)); }
-__device__ __forceinline__ int slice_tile_n(int Jp) { return (int)(blockIdx.x % (unsigned)(Jp / SBN)); }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
-// The GEMM main loop of tile (slice_tile_m, slice_tile_n) over SLICES A planes
-// [SLICES][Np][Kp] and B planes [SLICES][Jp][Kp] (Jp a multiple of SBN, Kp of
-// BK, Kp <= S_MAX_K).  The epilogue functor gets (column block c of 32,
-// t[32], em[32]) with t the joined accumulators and em the sum of the
-// magnitudes of the four rounded partial sums.  Returns false (all
-// threads) if a wait ran out.
+__device__ __forceinline__ int vload(const int& v) { return *(volatile const int*)&v; }
+
+// Tiles of the slice GEMM: (Np / BM) * (Jp / SBN) tiles numbered with the
+// column tile varying fastest, so that CTAs working at the same time share
+// their A slices through L2.  tile_m = t / (Jp / SBN), tile_n = t % (Jp / SBN).
+
+// The slice GEMM over SLICES A planes [SLICES][Np][Kp] and B planes
+// [SLICES][Jp][Kp] (Jp a multiple of SBN, Kp of BK, Kp <= S_MAX_K), every tile
+// of the grid-stride walk.  Launch with S_THREADS threads and S_SMEM_BYTES of
+// dynamic shared memory.  The epilogue functor gets epi.tile(tile_m, tile_n,
+// row in tile) at the start of each tile, then (column block c of 32, t[32],
+// em[32]) with t the joined accumulators and em the sum of the magnitudes of
+// the three rounded partial sums.  Every wait is bounded; returns false (all
+// threads) if one ran out.
 template <class Epi>
-__device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const CUtensorMap* tmB,
-                                                 const GemmArgs& a, Epi& epi)
+__device__ __forceinline__ bool gemm_sliced_persistent(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                                       const GemmArgs& a, Epi& epi)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2 * STAGES + 1];
+    // full[STAGES] | empty[STAGES] | tmem full[2] | tmem empty[2] | done
+    __shared__ __align__(8) uint64_t bars[2 * STAGES + 5];
     __shared__ uint32_t tmem_slot;
     __shared__ int failed;
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = slice_tile_m(a.Jp) * BM, n0 = slice_tile_n(a.Jp) * SBN;
+    const int nJt = a.Jp / SBN;
+    const int ntiles = (a.Np / BM) * nJt;
     const int nkb = a.Kp / BK;
     const uint32_t sbase = smem_u32(smem);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
     auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
-    const uint32_t done = smem_u32(&bars[2 * STAGES]);
+    auto tfull = [&](int b) { return smem_u32(&bars[2 * STAGES + b]); };
+    auto tempty = [&](int b) { return smem_u32(&bars[2 * STAGES + 2 + b]); };
+    const uint32_t done = smem_u32(&bars[2 * STAGES + 4]);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1);
+            mbar_init(tempty(b), 4);   // one arrival per epilogue warp
+        }
         mbar_init(done, 1);
         fence_mbar_init();
         failed = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(smem_u32(&tmem_slot), S_TMEM_COLS);
         tmem_relinquish();
     }
@@ -483,105 +507,147 @@ __device__ __forceinline__ bool gemm_tile_sliced(const CUtensorMap* tmA, const C
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer: per K block, the four A slices and the four B slices
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(empty(s), (uint32_t)((kb / STAGES - 1) & 1))) {
-                failed = 1;
-                break;
-            }
-            mbar_expect_tx(full(s), S_STAGE_BYTES);
-            const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
-            for (int p = 0; p < SLICES; ++p) {
-                tma_load_2d(st + (uint32_t)(p * S_A_BYTES), tmA, kb * BK, p * a.Np + m0, full(s));
-                tma_load_2d(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES), tmB, kb * BK, p * a.Jp + n0,
-                            full(s));
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: per K block, the four A slices and the four B
+            // slices; `it` counts K blocks over all tiles of this CTA
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !vload(failed); tile += gridDim.x) {
+                const int m0 = (tile / nJt) * BM, n0 = (tile % nJt) * SBN;
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !mbar_wait(empty(s), (uint32_t)((it / STAGES - 1) & 1))) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(full(s), S_STAGE_BYTES);
+                    const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
+                    for (int p = 0; p < SLICES; ++p) {
+                        tma_load_2d(st + (uint32_t)(p * S_A_BYTES), tmA, kb * BK, p * a.Np + m0, full(s));
+                        tma_load_2d(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES), tmB, kb * BK,
+                                    p * a.Jp + n0, full(s));
+                    }
+                }
+                if (!ok) break;
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: the ten slice products into the six accumulators
-        constexpr uint32_t idesc = idesc_bf16(BM, SBN);
-        bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(full(s), (uint32_t)((kb / STAGES) & 1))) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: the ten slice products into the four accumulators of
+            // the tile's accumulator set (tiles alternate between the two)
+            constexpr uint32_t idesc = idesc_bf16(BM, SBN);
+            // (A slice, B slice, accumulator); the first product of each
+            // accumulator starts it at the tile's first K step
+            constexpr int PA[SPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+            constexpr int PB[SPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+            constexpr int PACC[SPAIRS] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3};
+            constexpr int PLEAD[SPAIRS] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0};
+            int it = 0, tl = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !vload(failed); tile += gridDim.x, ++tl) {
+                const int buf = tl & 1;
+                if (tl >= 2 && !mbar_wait(tempty(buf), (uint32_t)(((tl >> 1) - 1) & 1))) {
+                    failed = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t accs = tmem + (uint32_t)(buf * S_ACC_COLS);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    if (!mbar_wait(full(s), (uint32_t)((it / STAGES) & 1))) {
+                        failed = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < BK / 16; ++ks) {
+                        const uint32_t off = (uint32_t)(ks * 32);   // 16 bf16 along K
+                        uint64_t ad[SLICES], bd[SLICES];
+#pragma unroll
+                        for (int p = 0; p < SLICES; ++p) {
+                            ad[p] = sdesc_sw128(st + (uint32_t)(p * S_A_BYTES) + off);
+                            bd[p] = sdesc_sw128(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES) + off);
+                        }
+                        const uint32_t first = (kb | ks) ? 1u : 0u;
+#pragma unroll
+                        for (int q = 0; q < SPAIRS; ++q)
+                            mma_bf16(accs + (uint32_t)(PACC[q] * SBN), ad[PA[q]], bd[PB[q]], idesc,
+                                     PLEAD[q] ? first : 1u);
+                    }
+                    mma_commit(empty(s));      // the stage is free once these MMAs are done
+                }
+                if (!ok) break;
+                mma_commit(tfull(buf));        // the tile's accumulators are complete
+            }
+            // every MMA issued by this thread has completed once `done` fires
+            mma_commit(done);
+            if (!mbar_wait(done, 0u)) failed = 1;
+        }
+    } else {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, one
+        // particle per lane
+        const int qtr = warp & 3;
+        const int row = 32 * qtr + lane;
+        const uint32_t lane_base = (uint32_t)(32 * qtr) << 16;
+        int tl = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+            const int buf = tl & 1;
+            const bool ok = mbar_wait(tfull(buf), (uint32_t)((tl >> 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
                 failed = 1;
-                ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t st = sbase + (uint32_t)(s * S_STAGE_BYTES);
-#pragma unroll
-            for (int ks = 0; ks < BK / 16; ++ks) {
-                const uint32_t off = (uint32_t)(ks * 32);   // 16 bf16 along K
-                uint64_t ad[SLICES], bd[SLICES];
-#pragma unroll
-                for (int p = 0; p < SLICES; ++p) {
-                    ad[p] = sdesc_sw128(st + (uint32_t)(p * S_A_BYTES) + off);
-                    bd[p] = sdesc_sw128(st + (uint32_t)(SLICES * S_A_BYTES + p * S_B_BYTES) + off);
-                }
-                const uint32_t first = (kb | ks) ? 1u : 0u;
-                // (accumulator, A slice, B slice); the first product of each
-                // accumulator starts it at the first K step
-                constexpr int PA[SPAIRS] = {0, 0, 1, 0, 2, 1, 0, 3, 1, 2};
-                constexpr int PB[SPAIRS] = {0, 1, 0, 2, 0, 1, 3, 0, 2, 1};
-                constexpr int PACC[SPAIRS] = {0, 1, 1, 2, 2, 3, 4, 4, 5, 5};
-                constexpr int PLEAD[SPAIRS] = {1, 1, 0, 1, 0, 1, 1, 0, 1, 0};
-#pragma unroll
-                for (int q = 0; q < SPAIRS; ++q)
-                    mma_bf16(tmem + (uint32_t)(PACC[q] * SBN), ad[PA[q]], bd[PB[q]], idesc, PLEAD[q] ? first : 1u);
-            }
-            mma_commit(empty(s));      // the stage is free once these MMAs are done
-        }
-        mma_commit(done);              // all MMAs issued (possibly none if a wait failed)
-    }
-    __syncwarp();
-
-    bool ok = mbar_wait(done, 0u);
-    if (!ok) failed = 1;
-    tc_fence_after();
-    __syncthreads();
-    const bool good = !failed;
-    if (good) {
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            const uint32_t accs = tmem + lane_base + (uint32_t)(buf * S_ACC_COLS);
+            epi.tile(tile / nJt, tile % nJt, row);
 #pragma unroll 1
-        for (int c = 0; c < SBN / 32; ++c) {
-            float t[32], em[32], v[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(4 * SBN + 32 * c), t);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                t[q] = __fmul_rn(t[q], 0x1p-21f);   // exact
-                em[q] = 0.f;
-            }
-            // (accumulator, weight) from the smallest weight up; each step one
-            // rounding (the scaled accumulator is exact)
-            constexpr int JA[4] = {5, 3, 2, 1};
-            constexpr float JW[4] = {0x1p-21f, 0x1p-14f, 0x1p-14f, 0x1p-7f};
-#pragma unroll
-            for (int st = 0; st < 4; ++st) {
-                tmem_ld32(tmem + lane_base + (uint32_t)(JA[st] * SBN + 32 * c), v);
+            for (int c = 0; c < SBN / 32; ++c) {
+                float t[32], em[32], v[32];
+                tmem_ld32(accs + (uint32_t)(3 * SBN + 32 * c), t);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
-                    t[q] = __fmaf_rn(v[q], JW[st], t[q]);
+                    t[q] = __fmul_rn(t[q], 0x1p-21f);   // exact
+                    em[q] = 0.f;
+                }
+                // (accumulator, weight) from the smallest weight up; each step one
+                // rounding (the scaled accumulator is exact)
+                constexpr int JA[2] = {2, 1};
+                constexpr float JW[2] = {0x1p-14f, 0x1p-7f};
+#pragma unroll
+                for (int st = 0; st < 2; ++st) {
+                    tmem_ld32(accs + (uint32_t)(JA[st] * SBN + 32 * c), v);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        t[q] = __fmaf_rn(v[q], JW[st], t[q]);
+                        em[q] = __fadd_ru(em[q], fabsf(t[q]));
+                    }
+                }
+                tmem_ld32(accs + (uint32_t)(32 * c), v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    t[q] = __fadd_rn(v[q], t[q]);
                     em[q] = __fadd_ru(em[q], fabsf(t[q]));
                 }
+                epi(c, t, em);
             }
-            tmem_ld32(tmem + lane_base + (uint32_t)(32 * c), v);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                t[q] = __fadd_rn(v[q], t[q]);
-                em[q] = __fadd_ru(em[q], fabsf(t[q]));
-            }
-            epi(c, t, em);
+            // the accumulator set may be overwritten once all four warps have read it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(buf));
         }
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, S_TMEM_COLS);
     }
+    const bool good = !vload(failed);
     if (!good && threadIdx.x == 0 && a.status) atomicExch(a.status, 1);
     return good;
 }

@@ -1,25 +1,24 @@
 """The arithmetic of the tensor pipeline's exact integer-slice GEMM, restated
 in numpy on the CPU: the slice scale, the four 7-bit slices of an exact float
 pair (d = x - o) and of an FP64 value (M), and the facts the bound rests on --
-|V0| <= 127, |V1..V3| <= 64, the rest within 1.01 2^-29, the six
-accumulators' products summing per k to at most 16129 / 16256 / 16256 / 4096 /
-16256 / 8192 so that K = 1024 partial sums stay below 2^24, and the dropped
-products of weight 4..6 with the remainders within the per-k bound of the
-epilogue."""
+|V0..V3| <= 64, the rest within 1.01 2^-29, the four accumulators (one per
+weight) gaining per k at most 4096 / 8192 / 12288 / 16384 so that partial sums
+over D <= 1023 terms stay below 2^24, and the dropped products of weight 4..6
+with the remainders within the per-k bound of the epilogue."""
 import numpy as np
 
 F = np.float32
 SLICE_DROP = 3.04 * 2.0 ** -30
 SLICE_REM = 1.01 * 2.0 ** -29
 # (A slice, B slice) pairs of each accumulator, its weight, its per-k maximum
-ACCS = [([(0, 0)], 0, 16129), ([(0, 1), (1, 0)], 1, 16256), ([(0, 2), (2, 0)], 2, 16256),
-        ([(1, 1)], 2, 4096), ([(0, 3), (3, 0)], 3, 16256), ([(1, 2), (2, 1)], 3, 8192)]
+ACCS = [([(0, 0)], 0, 4096), ([(0, 1), (1, 0)], 1, 8192), ([(0, 2), (1, 1), (2, 0)], 2, 12288),
+        ([(0, 3), (1, 2), (2, 1), (3, 0)], 3, 16384)]
 
 
 def slice_scale(vmax):
     if not vmax > 0:
         return F(1.0)
-    m = F(F(F(vmax) * F(128.0 / 127.0)) * F(1 + 2.0 ** -20))
+    m = F(F(F(vmax) * F(2.0)) * F(1 + 2.0 ** -20))
     _, e = np.frexp(m)
     return F(np.ldexp(1.0, int(e)))
 
@@ -88,15 +87,15 @@ def test_slices_reconstruct_within_remainder_bound():
     rng = np.random.default_rng(7)
     for hi, lo, exact in _d_rows(rng, 20, 129):
         sd, S, _ = _d_slices(hi, lo)
-        assert np.abs(exact).max() <= 127 / 128 * sd
-        assert np.all(np.abs(S[:, 0]) <= 127) and np.all(np.abs(S[:, 1:]) <= 64)
+        assert np.abs(exact).max() < sd / 2
+        assert np.all(np.abs(S) <= 64)
         rec = S @ (128.0 ** -np.arange(1, 5))
         assert np.all(np.abs(exact / sd - rec) <= SLICE_REM)
     for _ in range(20):
         m = rng.standard_normal(129) * 10.0 ** rng.uniform(-4, 1)
         sm, S = _m_slices(m)
-        assert np.abs(m).max() <= 127 / 128 * sm
-        assert np.all(np.abs(S[:, 0]) <= 127) and np.all(np.abs(S[:, 1:]) <= 64)
+        assert np.abs(m).max() < sm / 2
+        assert np.all(np.abs(S) <= 64)
         assert np.all(np.abs(m / sm - S @ (128.0 ** -np.arange(1, 5))) <= SLICE_REM)
 
 
@@ -118,3 +117,18 @@ def test_accumulators_exact_and_dropped_terms_bounded():
             dropped = np.abs(exact * m - kept * sd * sm)
             bound = SLICE_DROP * sd * sm + SLICE_REM * (sm * np.abs(exact) + sd * np.abs(m))
             assert np.all(dropped <= bound * (1 + 1e-9))
+
+
+def test_extreme_slices_and_worst_case_partial_sums():
+    """Entries at the row maximum give a top slice of magnitude 64, never
+    more; with every slice at 64 the per-k gains of the four accumulators are
+    1, 2, 3 and 4 products of 4096, and over D <= 1023 terms the partial sums
+    stay below 2^24 (with D = 1024 the last could reach it, hence the limit)."""
+    m = np.array([1.99, -1.99, 1.9921875, 0.25, -1e-9, 0.0])
+    sm, S = _m_slices(m)
+    assert sm == 4.0 and np.abs(m).max() < sm / 2 and np.all(np.abs(S) <= 64)
+    assert np.abs(S[:, 0]).max() == 64
+    for pairs, _, cap in ACCS:
+        assert cap == 4096 * len(pairs)
+        assert cap * 1023 < 2 ** 24
+    assert max(cap for _, _, cap in ACCS) * 1024 == 2 ** 24
