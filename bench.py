@@ -326,13 +326,18 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
+REFINE_KERNELS = ("z32", "fix32", "z64", "fix64", "z64_argmin", "fix64_argmin")
+
+
+def tensor_roofline(psso, problems, prec, sptr, workload, t_gens, gens=20):
     """Rotated swarms on the tensor-core pipeline: per-kernel event timing of
     the first such instance (psso_time_kernels) and the roofline of the GEMM
     kernel.  Algorithmic work is z = M (x - o): 2 N D^2 flops per generation;
     the kernel executes ten BF16 slice products (four 7-bit integer slices per
-    operand, weights 0..3, in six exact accumulators) over the padded
-    extents."""
+    operand, weights 0..3, in four exact accumulators) over the padded
+    extents.  Each instance is timed early (generations gens+1 .. 2 gens,
+    many close decisions) and again around generation t_gens / 2; the share of
+    the refinement and FP64 kernels in a generation is reported for both."""
     rot = [p for p in problems if p["fn"].startswith("rot_") and p["N"] >= 128 and p["D"] >= 32]
     if prec != "f32" or not rot:
         return None
@@ -341,7 +346,14 @@ def tensor_roofline(psso, problems, prec, sptr, workload, gens=20):
         h = psso.psso_create_ex([q], prec, stream=sptr)
         try:
             psso.psso_run(h, gens)
-            per_instance.append({"fn": q["fn"], "kernels_ms": psso.psso_time_kernels(h, 0, gens)})
+            early = psso.psso_time_kernels(h, 0, gens)
+            late_at = max(t_gens // 2, 3 * gens)
+            psso.psso_run(h, late_at - 2 * gens)
+            late = psso.psso_time_kernels(h, 0, gens)
+            share = {k: sum(v for n, v in ms.items() if n in REFINE_KERNELS) / sum(ms.values())
+                     for k, ms in (("early", early), ("late", late))}
+            per_instance.append({"fn": q["fn"], "kernels_ms": early, "kernels_ms_late": late,
+                                 "late_generation": late_at, "refine_share": share})
         finally:
             psso.psso_destroy(h)
     p = rot[0]
@@ -714,7 +726,7 @@ def main():
     if n_bat and st["blocks"] == 0:
         roofline = batched_roofline(psso, problems, prec, t, sptr, live, args.workload)
     else:
-        roofline = tensor_roofline(psso, problems, prec, sptr, args.workload)
+        roofline = tensor_roofline(psso, problems, prec, sptr, args.workload, t)
     if roofline is None:
         per_lane = -(-(-(-p0["D"] // 4)) // 32)          # chunks of 4 variables per lane
         width = 1 if per_lane <= 1 else 2 if per_lane <= 2 else 4 if per_lane <= 4 else 8

@@ -356,14 +356,19 @@ __global__ void rot_decide(const RotDev r)
 }
 
 // ---- 4. refinement: compensated FP32 rotation of list-1 rows ---------------------------
-// d = x - o exactly as a float pair (TwoSum), M = Mh + Ml.  One warp per
-// output j, lane l taking k = l, l + 32, ... (coalesced rows of M): the Dot2
+// d = x - o exactly as a float pair (TwoSum), M = Mh + Ml.  Per output j the
+// 32 lanes of a warp take k = l, l + 32, ... (coalesced rows of M): the Dot2
 // recurrence per lane (TwoProduct of Mh d_h, TwoSum into p, the rounding
 // errors and the cross terms Mh d_l + Ml d_h into s), then the 32 lane sums
 // merged by a TwoSum butterfly, z = p + s.  With n = ceil(D / 32) + 8 and
 // g = gamma_n: |z~ - z| <= 1.01 u |z~| + (2 g^2 + 4 u g + 2^-42) S, where
 // S = sum |M||d| <= S~ (1 + 2 gamma_D)(1 + 2^-22) from the FP32 sum S~ of
 // |Mh||d_h|; 2^-42 S also covers the oracle's own FP64 rounding of z.
+// A block takes Z32_OUT outputs of one listed row; each warp keeps Z32_NJ
+// outputs in flight (independent chains sharing the loads of d), so a short
+// list still spreads over many blocks and the loads of M overlap.
+constexpr int Z32_NJ = 4;                       // outputs per warp in flight
+constexpr int Z32_OUT = 32;                     // outputs per block
 __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
 {
     __shared__ float dh[1024], dl[1024];
@@ -372,7 +377,7 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
     const int D = r.D;
     if (!PSSO_CHK(n <= r.N && D <= 1024, CHK_LIST, n)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nJb = (D + 127) / 128;
+    const int nJb = (D + Z32_OUT - 1) / Z32_OUT;
     const float U = 0x1p-24f;
     const float nl = (float)((D + 31) / 32 + 8);
     const float gam = nl * U / (1.f - nl * U);
@@ -397,45 +402,62 @@ __global__ void __launch_bounds__(128) rot_z32(const RotDev r)
         }
         __syncthreads();
         const size_t o = (size_t)(2 * e + row) * d.Dp;
-        for (int t = 0; t < 32; ++t) {
-            const int j = jb * 128 + warp * 32 + t;
-            if (j >= D) {
-                if (j < d.Dp && lane == 0) {
-                    r.z32[o + j] = 0.f;
-                    r.ez32[o + j] = 0.f;
-                }
-                continue;
+#pragma unroll 1
+        for (int pass = 0; pass < Z32_OUT / (4 * Z32_NJ); ++pass) {
+            const int j0 = jb * Z32_OUT + pass * 4 * Z32_NJ + warp * Z32_NJ;   // warp-uniform
+            int nv = D - j0;                     // outputs of this group inside the row
+            nv = nv < 0 ? 0 : nv > Z32_NJ ? Z32_NJ : nv;
+            if (lane == 0)
+                for (int t = nv; t < Z32_NJ; ++t)
+                    if (j0 + t < d.Dp) {
+                        r.z32[o + j0 + t] = 0.f;
+                        r.ez32[o + j0 + t] = 0.f;
+                    }
+            if (nv == 0) continue;
+            const float* mh[Z32_NJ];
+            const float* ml[Z32_NJ];
+            float p[Z32_NJ], sc[Z32_NJ], S[Z32_NJ];
+#pragma unroll
+            for (int t = 0; t < Z32_NJ; ++t) {
+                const int j = t < nv ? j0 + t : j0;   // rows past the end repeat a valid one, unused
+                mh[t] = r.Mh + (size_t)j * D;
+                ml[t] = r.Ml + (size_t)j * D;
+                p[t] = sc[t] = S[t] = 0.f;
             }
-            const float* mh = r.Mh + (size_t)j * D;
-            const float* ml = r.Ml + (size_t)j * D;
-            float p = 0.f, sc = 0.f, S = 0.f;
             for (int k = lane; k < D; k += 32) {
-                const float a = __ldg(mh + k), b = dh[k];
-                const float h = __fmul_rn(a, b);
-                const float rr = __fmaf_rn(a, b, -h);                 // a b = h + rr exactly
-                const float tt = __fadd_rn(p, h);
-                const float bb = __fsub_rn(tt, p);
-                const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(tt, bb)), __fsub_rn(h, bb));   // p + h = tt + q
-                p = tt;
-                const float cross = __fmaf_rn(a, dl[k], __fmul_rn(__ldg(ml + k), b));
-                sc = __fadd_rn(sc, __fadd_rn(__fadd_rn(q, rr), cross));
-                S = __fmaf_rn(fabsf(a), fabsf(b), S);
+                const float b = dh[k], bl = dl[k];
+#pragma unroll
+                for (int t = 0; t < Z32_NJ; ++t) {
+                    const float a = __ldg(mh[t] + k);
+                    const float h = __fmul_rn(a, b);
+                    const float rr = __fmaf_rn(a, b, -h);                 // a b = h + rr exactly
+                    const float tt = __fadd_rn(p[t], h);
+                    const float bb = __fsub_rn(tt, p[t]);
+                    const float q = __fadd_rn(__fsub_rn(p[t], __fsub_rn(tt, bb)), __fsub_rn(h, bb));   // p + h = tt + q
+                    p[t] = tt;
+                    const float cross = __fmaf_rn(a, bl, __fmul_rn(__ldg(ml[t] + k), b));
+                    sc[t] = __fadd_rn(sc[t], __fadd_rn(__fadd_rn(q, rr), cross));
+                    S[t] = __fmaf_rn(fabsf(a), fabsf(b), S[t]);
+                }
             }
-            for (int off = 16; off > 0; off >>= 1) {       // every lane ends with the same values
-                const float po = __shfl_xor_sync(0xffffffffu, p, off);
-                const float so = __shfl_xor_sync(0xffffffffu, sc, off);
-                const float Sq = __shfl_xor_sync(0xffffffffu, S, off);
-                const float tt = __fadd_rn(p, po);
-                const float bb = __fsub_rn(tt, p);
-                const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(tt, bb)), __fsub_rn(po, bb));
-                p = tt;
-                sc = __fadd_rn(__fadd_rn(sc, so), q);
-                S = __fadd_rn(S, Sq);
-            }
-            if (lane == 0) {
-                const float z = __fadd_rn(p, sc);
-                r.z32[o + j] = z;
-                r.ez32[o + j] = __fmaf_ru(cS, S, 1.01f * U * fabsf(z));
+#pragma unroll
+            for (int t = 0; t < Z32_NJ; ++t) {
+                for (int off = 16; off > 0; off >>= 1) {       // every lane ends with the same values
+                    const float po = __shfl_xor_sync(0xffffffffu, p[t], off);
+                    const float so = __shfl_xor_sync(0xffffffffu, sc[t], off);
+                    const float Sq = __shfl_xor_sync(0xffffffffu, S[t], off);
+                    const float tt = __fadd_rn(p[t], po);
+                    const float bb = __fsub_rn(tt, p[t]);
+                    const float q = __fadd_rn(__fsub_rn(p[t], __fsub_rn(tt, bb)), __fsub_rn(po, bb));
+                    p[t] = tt;
+                    sc[t] = __fadd_rn(__fadd_rn(sc[t], so), q);
+                    S[t] = __fadd_rn(S[t], Sq);
+                }
+                if (lane == 0 && t < nv) {
+                    const float z = __fadd_rn(p[t], sc[t]);
+                    r.z32[o + j0 + t] = z;
+                    r.ez32[o + j0 + t] = __fmaf_ru(cS, S[t], 1.01f * U * fabsf(z));
+                }
             }
         }
     }
