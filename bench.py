@@ -292,7 +292,7 @@ def job_rate(units_per_step, steps, world, max_total_ms):
 # digest of the kernel's sources at capture time and is reported only while
 # the sources still match (a changed kernel reports traffic null).
 TRAFFIC = {
-    ("rot_gemm_fit", "rotated_d1000"): ("e711260c0d4da450", 75.650816e6 + 3.425024e6),
+    ("rot_gemm_fit", "rotated_d1000"): ("0b1474d8c773c520", 75.650048e6 + 2.041344e6),
     ("sso_generations", "rastrigin_d100"): ("c5a611e6e84c4e41", 1.407488e6 + 0.055552e6),
     ("bat_stream", "batched_512"): ("b96e79894cdf97df", 668.860928e6 + 913.625856e6),
 }
