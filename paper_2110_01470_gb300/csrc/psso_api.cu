@@ -929,8 +929,8 @@ psso_status create_impl(const psso_problem* problems, int32_t count, const psso_
         if (rot) I.M.assign(I.pr.rotation, I.pr.rotation + I.pr.D * I.pr.D);
         I.pr.shift = I.pr.weights = I.pr.rotation = nullptr;
         I.tc = h->precision == PSSO_PREC_F32_RECHECK && rot &&
-               (c.tensor_rotation == 1 || (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32)) &&
-               I.pr.D <= tc::S_MAX_D;
+               (c.tensor_rotation == 1 ||
+                (c.tensor_rotation == 0 && I.pr.N >= 128 && I.pr.D >= 32 && I.pr.D <= tc::S_MAX_D));
     }
     {
         int n_plain = 0;

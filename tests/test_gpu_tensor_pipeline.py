@@ -162,3 +162,23 @@ def test_time_kernels_keeps_the_trajectory(lib):
             lib.psso_time_kernels(h, 0, 2)
     finally:
         lib.psso_destroy(h)
+
+
+@pytest.mark.parametrize("fn", ["rot_ellipsoid", "rot_rastrigin"])
+def test_largest_exact_extent(lib, fn):
+    """D = 1023 is the largest extent at which the slice GEMM's partial sums stay
+    below 2^24 with every slice at its bound (64): the pipeline runs it with the
+    oracle's decisions.  D = 1024 is refused when the pipeline is forced and runs
+    on the per-particle kernel in the automatic mode."""
+    t = 3
+    p = workload.problem(fn, 130, 1023, seed=9, lattice="f32")
+    (g,), st = _run(lib, [p], t)
+    _same(g, _oracle(p, t), t, fn)
+    assert st["blocks"] == 0
+    q = workload.problem(fn, 130, 1024, seed=9, lattice="f32")
+    with pytest.raises(lib.PssoError) as exc:
+        lib.psso_create_ex([q], "f32", tensor_rotation=1)
+    assert exc.value.status == lib.PSSO_ERR_UNSUPPORTED
+    (g,), st = _run(lib, [q], 2, tensor_rotation=0)
+    assert st["blocks"] > 0
+    _same(g, _oracle(q, 2), 2, fn)
